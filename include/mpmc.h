@@ -1,0 +1,246 @@
+/*
+ * mpmc.h -- C ABI of the GB300 hot path of Multipolynomial Monte Carlo
+ * (Lashomb, Morgan, Whyte, Wilcox, arXiv:2306.09559).
+ *
+ * The library estimates the traces of the multilevel decomposition of
+ * Sec. 3.1, Eq. (2), with polynomials p_j(A) of the Wilson-Dirac matrix
+ * A = I - kappa*H applied to blocks of Z4 noise vectors (Sec. 1) in root
+ * form (Sec. 2.3), composite ("double") polynomials (Secs. 2.4, 3.2) and
+ * eigenvector deflation of the polynomial-difference levels (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are two consecutive doubles (re, im).
+ *  - dims = {Lx, Ly, Lz, Lt}, each >= 2.  V = Lx*Ly*Lz*Lt sites, n = 12 V.
+ *  - Site index s = ((t*Lz + z)*Ly + y)*Lx + x; unknown index within a
+ *    site e = spin*3 + colour (spin 0..3, colour 0..2).
+ *  - Links: U[mu][s][a][b], mu = 0..3 for x, y, z, t, each a 3x3 complex
+ *    matrix (row a, column b): 4*V*9 complex = 72 V doubles.
+ *  - A = I - kappa * sum_mu [(1 - gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                           + (1 + gamma_mu) U_mu(x-mu)^+ delta_{x-mu,y}]
+ *    with Hermitian gamma matrices in the chiral DeGrand-Rossi basis,
+ *    gamma5 = diag(1, 1, -1, -1); periodic boundaries (bc_t = -1 makes the
+ *    t direction antiperiodic).  The paper names the matrix only
+ *    ("quenched Wilson-Dirac", Sec. 5, Examples 2 and 3); this is the
+ *    reading every part of the project uses.
+ *  - Vector blocks passed to mpmc_apply_*: complex doubles laid out
+ *    [s][e][r] (right-hand side r innermost), i.e. element (unknown
+ *    12 s + e, column r) at offset (12 s + e) * nrhs + r complex numbers.
+ *  - Z4 noise (Sec. 1): vector j of level l has entry e of site s equal to
+ *    i^q, q = bits 2e..2e+1 of word 0 of Philox-4x32-10 (Salmon et al.,
+ *    SC'11) with key (seed & 0xffffffff, seed >> 32) and counter
+ *    (j, s, l, 0).
+ *
+ * Ownership: every input is copied into library-owned device memory
+ * before the call returns; the caller keeps its buffers.  Calls on one
+ * handle must not overlap (a handle is not thread-safe); different handles
+ * are independent.  All work is enqueued on the handle's stream (its own,
+ * or the one given by mpmc_set_stream); calls that return host results
+ * synchronise that stream.
+ *
+ * Errors: every call returns MPMC_OK (0) or a positive code below.  No
+ * call aborts the process.  mpmc_last_error() gives a message for the last
+ * failing call on a handle.
+ */
+#ifndef MPMC_H
+#define MPMC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MPMC_API __attribute__((visibility("default")))
+#else
+#define MPMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpmc_ctx* mpmc_handle;
+
+enum {
+    MPMC_OK = 0,
+    MPMC_EINVAL = 1,      /* bad argument: dims < 2, kappa not finite, nroots < 1, k > n, ... */
+    MPMC_ENOMEM = 2,      /* device or host allocation failed */
+    MPMC_ENOTSUP = 3,     /* precision or mode not supported */
+    MPMC_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    MPMC_ENONFINITE = 5,  /* a non-finite root, eigenvalue or sample */
+    MPMC_ECUDA = 6,       /* a CUDA runtime call failed (message in mpmc_last_error) */
+    MPMC_ESTATE = 7       /* call out of order: e.g. trace before any polynomial is set */
+};
+
+/* Arithmetic of the stencil and polynomial chain. */
+enum {
+    MPMC_FP64 = 0,   /* FP64 vectors, links and arithmetic */
+    MPMC_FP32 = 1,   /* FP32 vectors and links, FP32 arithmetic, FP64 b^H x accumulation */
+    MPMC_BF16S = 2   /* BF16-stored vectors, FP32 links and arithmetic, FP64 accumulation */
+};
+
+/* Polynomial kinds (mpmc_set_poly). */
+enum {
+    MPMC_SINGLE = 0,             /* p(A) from one GMRES run, Secs. 2.3, 3.1 */
+    MPMC_COMPOSITE = 1,          /* p_in(A) p_out(A p_in(A)), Secs. 2.4, 3.2 */
+    MPMC_DEFLATED_COMPOSITE = 2  /* projection then composite, Sec. 4.3 */
+};
+
+/*
+ * mpmc_create: a handle for one lattice.  links: host array described
+ * above (copied).  kappa: hopping parameter (finite).  precision: one of
+ * MPMC_FP64/FP32/BF16S.  bc_t: +1 periodic or -1 antiperiodic in t.
+ * Defines the matrix A of Secs. 1 and 5 (see the conventions).
+ * Errors: EINVAL (dims, kappa, bc_t), ENOTSUP (precision), ENOMEM, ECUDA.
+ * *h is NULL on failure.
+ */
+MPMC_API int mpmc_create(mpmc_handle* h, const int dims[4], const double* links,
+                double kappa, int precision, int bc_t);
+
+/* mpmc_destroy: frees all device memory of the handle; NULL is accepted. */
+MPMC_API int mpmc_destroy(mpmc_handle h);
+
+/* mpmc_strerror: static text for an error code. */
+MPMC_API const char* mpmc_strerror(int code);
+
+/* mpmc_last_error: message of the last failing call on h (never NULL). */
+MPMC_API const char* mpmc_last_error(mpmc_handle h);
+
+/*
+ * mpmc_set_stream: enqueue all further work of h on the CUDA stream
+ * `stream` (a cudaStream_t, owned by the caller, which must outlive its
+ * use); NULL restores the handle's own stream.
+ */
+MPMC_API int mpmc_set_stream(mpmc_handle h, void* stream);
+
+/*
+ * mpmc_set_block: number of right-hand sides processed per launch
+ * (1..MPMC_MAX_BLOCK).  0 restores the default.  Only performance depends
+ * on it: samples and applied vectors do not.
+ */
+#define MPMC_MAX_BLOCK 1024
+MPMC_API int mpmc_set_block(mpmc_handle h, int nrhs_block);
+
+/*
+ * mpmc_set_poly: polynomial number `index` (0 <= index < MPMC_MAX_POLYS).
+ * roots: nroots complex values theta_1..theta_m, the harmonic Ritz values
+ * of the GMRES run that defines p through pi(alpha) = 1 - alpha p(alpha)
+ * (Sec. 3.1); p has degree m - 1 and is applied in root form
+ * p(A) v = sum_i theta_i^{-1} prod_{j<i} (I - A/theta_j) v (Sec. 2.3).
+ * For the composite kinds, roots are those of p_in and outer (nouter
+ * values) those of p_out, found by GMRES on A p_in(A); the polynomial is
+ * p_in(A) p_out(A p_in(A)) of degree nroots*nouter - 1 (Sec. 3.2).  The
+ * deflated kind adds the projection of Sec. 4.3 with the eigenpairs of
+ * mpmc_set_deflation (which must be called first).
+ * leja != 0 reorders each root list into modified Leja order (first the
+ * root of largest modulus, then each next root maximising the product of
+ * distances to those taken; ties to the lowest index); leja = 0 keeps the
+ * caller's order.
+ * Polynomials 0..L-1 define the levels of mpmc_trace_levels: level l < L-1
+ * is Tr(p_l - p_{l+1}), level L-1 is Tr(p_{L-1}) (Eq. (2)).
+ * Errors: EINVAL (index, kind, counts, NULL roots), ENONFINITE (a root is
+ * zero or not finite), ESTATE (deflated kind without deflation).
+ */
+#define MPMC_MAX_POLYS 8
+MPMC_API int mpmc_set_poly(mpmc_handle h, int index, int kind,
+                  const double* roots, int nroots,
+                  const double* outer, int nouter, int leja);
+
+/* mpmc_get_roots: copies the (possibly reordered) roots of polynomial
+ * `index` to roots[0..2*nroots) and outer[0..2*nouter) (either may be
+ * NULL).  Errors: EINVAL, ESTATE (not set). */
+MPMC_API int mpmc_get_roots(mpmc_handle h, int index, double* roots, double* outer);
+
+/*
+ * mpmc_set_deflation: eigenpairs for the Monte Carlo deflation of Sec. 4.1
+ * and the projection of Sec. 4.3.  Z: host, k right eigenvectors, vector i
+ * at Z + 2*n*i (complex, unknown order); lambda: k complex eigenvalues;
+ * pair[i] = j says the left eigenvector of lambda_i is gamma5 z_j (j = i
+ * for real lambda_i, the conjugate partner otherwise; Sec. 4).  The
+ * library scales u_i so that u_i^H z_i = 1 using the vectors as stored in
+ * its working precision, so the exact correction sum_i c_i u_i^H z_i and
+ * the sampled term use the same vectors.  k = 0 removes the deflation.
+ * Errors: EINVAL (k < 0, k > n, pair out of range or not an involution,
+ * NULL pointers with k > 0), ENONFINITE (u_i^H z_i = 0 or NaN).
+ */
+MPMC_API int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda,
+                       const int* pair, int k);
+
+/*
+ * mpmc_apply_op: Y = A X for nrhs vectors in the block layout above.
+ * on_device != 0: X and Y are device pointers (complex double, same
+ * layout) usable on the handle's stream; otherwise host pointers.
+ * The product runs in the handle's precision.
+ */
+MPMC_API int mpmc_apply_op(mpmc_handle h, const double* X, double* Y, int nrhs, int on_device);
+
+/*
+ * mpmc_apply_poly: X = p_index(A) B (root form of Sec. 2.3, composite of
+ * Sec. 3.2, or the projected composite of Sec. 4.3), layout and on_device
+ * as for mpmc_apply_op.  Errors: EINVAL, ESTATE (polynomial not set).
+ */
+MPMC_API int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X,
+                    int nrhs, int on_device);
+
+/*
+ * mpmc_trace_levels: the Monte Carlo of every level (Eq. (2), Sec. 4.1).
+ * For level l and j = first .. first+nsamples-1 it draws Z4 noise b_j
+ * (level id l), and forms
+ *     s_j = b_j^H p_l(A) b_j - b_j^H p_{l+1}(A) b_j
+ *           - sum_i c_i (b_j^H z_i)(u_i^H b_j),   c_i = p_l(lambda_i) - p_{l+1}(lambda_i)
+ * (p_{l+1} = 0 and no deflation for the last level; c_i uses
+ * 1/lambda_i for a deflated composite).  Outputs (host, any may be NULL):
+ *   mean[2*l..2*l+1]   estimate = sample mean + sum_i c_i u_i^H z_i (complex)
+ *   var[l]             sample variance of Re s_j (unbiased)
+ *   samples[2*(l*nsamples + j) ...]   s_j (complex)
+ * nsamples >= 1 (variance needs >= 2; var = NaN for 1).
+ * Errors: EINVAL, ESTATE (no polynomial), ENONFINITE (a sample is not
+ * finite), ECUDA.
+ */
+MPMC_API int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first,
+                      double* mean, double* var, double* samples);
+
+/*
+ * mpmc_level_info: for level l, the exact deflation correction
+ * sum_i c_i u_i^H z_i (complex, 2 doubles) and the number of products with
+ * A per noise vector (the "MVP" count of Tables 1-8).  Either output may
+ * be NULL.  Errors: EINVAL, ESTATE.
+ */
+MPMC_API int mpmc_level_info(mpmc_handle h, int level, double* correction, long long* matvecs);
+
+/*
+ * mpmc_noise: writes noise vectors first .. first+nrhs-1 of level `level`
+ * as complex doubles in the block layout (host or device per on_device).
+ * The same bits the trace kernels regenerate internally.
+ */
+MPMC_API int mpmc_noise(mpmc_handle h, uint64_t seed, int level, int first, int nrhs,
+               double* B, int on_device);
+
+/*
+ * mpmc_arnoldi: m steps of FP64 Arnoldi with two passes of classical
+ * Gram-Schmidt on the operator A (op_poly < 0) or A p_{op_poly}(A)
+ * (the polynomial preconditioned operator of Secs. 2.3, 3.2, 4), started
+ * from the host vector v0 (n complex).  hbar (host, (m+1) x m complex,
+ * row-major, entry (i, j) at 2*(i*m + j)) receives the Hessenberg matrix;
+ * basis (device, n x (m+1) complex, vector j at basis + 2*n*j) receives the
+ * orthonormal basis when not NULL.  Used for the setup of Sec. 5, step 2.
+ * Returns the number of completed steps in *steps (< m on breakdown).
+ * All vector work is FP64 on the GPU whatever the handle's precision.
+ */
+MPMC_API int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m,
+                 double* hbar, double* basis, int* steps);
+
+/*
+ * mpmc_combine: Z = Vb * Y on the device in FP64: Vb n x m (device, vector
+ * j at Vb + 2*n*j), Y m x k (host, row-major complex), Z n x k (device,
+ * vector i at Z + 2*n*i).  Forms Ritz vectors from an Arnoldi basis.
+ */
+MPMC_API int mpmc_combine(mpmc_handle h, const double* Vb, int m, const double* Y, int k, double* Z);
+
+/* Device counter of kernel launches made by the library since the handle
+ * was created (the count a caller reports for its timed region). */
+MPMC_API long long mpmc_launch_count(mpmc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPMC_H */

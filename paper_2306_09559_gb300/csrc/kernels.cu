@@ -1,0 +1,606 @@
+// CUDA kernels of the GB300 hot path (sm_103a): the root-form polynomial
+// step fused into the multi-RHS Wilson stencil, the composite outer step,
+// the level-sample assembly, the deflation dot products, and the FP64
+// vector kernels of the Krylov setup.
+#include "device.cuh"
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace mpmc {
+
+namespace {
+
+template <class T> __device__ __forceinline__ cplx<T> cdv(const double (&v)[2]) { return {T(v[0]), T(v[1])}; }
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+NoiseKey make_key(const NoiseSpec& ns) {
+    NoiseKey k;
+    k.k0 = (uint32_t)(ns.seed & 0xffffffffu);
+    k.k1 = (uint32_t)(ns.seed >> 32);
+    k.level = ns.level;
+    k.j0 = ns.j0;
+    return k;
+}
+
+Lattice make_lat(const Geom& g) {
+    Lattice L;
+    L.lx = g.lx; L.ly = g.ly; L.lz = g.lz; L.lt = g.lt; L.V = g.V; L.bc_t = g.bc_t;
+    return L;
+}
+
+// Block reduction of a per-thread complex value over threadIdx.y (fixed
+// order), then acc[blockIdx.x][col] += w * sum by the threadIdx.y == 0 row.
+template <class T>
+__device__ __forceinline__ void cta_dot_accumulate(cplx<T> v, int col, bool colok, int nb, const double (&w)[2],
+                                                   double2* acc) {
+    __shared__ double2 red[256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    red[tid] = make_double2((double)v.re, (double)v.im);
+    __syncthreads();
+    if (threadIdx.y == 0 && colok) {
+        double sr = 0.0, si = 0.0;
+        for (int yy = 0; yy < (int)blockDim.y; ++yy) {
+            const double2 q = red[yy * blockDim.x + threadIdx.x];
+            sr += q.x;
+            si += q.y;
+        }
+        double2* pa = acc + (size_t)blockIdx.x * nb + col;
+        double2 cur = *pa;
+        cur.x += w[0] * sr - w[1] * si;
+        cur.y += w[0] * si + w[1] * sr;
+        *pa = cur;
+    }
+}
+
+// ------------------------------------------------------------------ step
+template <class S, bool NOISE_IN, bool DOT, int YMODE>
+__global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
+                                              int nb, NoiseKey nk, int sl) {
+    using T = typename Math<S>::T;
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool colok = col < nb;
+    const cplx<T> ca = cdv<T>(a.a), cc = cdv<T>(a.c), cya = cdv<T>(a.ya), cyb = cdv<T>(a.yb);
+    cplx<T> dsum = cz<T>();
+    const int base = blockIdx.x * blockDim.y * sl;
+    for (int it = 0; it < sl; ++it) {
+        const int site = base + it * blockDim.y + threadIdx.y;
+        if (site >= L.V || !colok) continue;
+        cplx<T> hw[12], own[12];
+        if (NOISE_IN) {
+            NoiseSource<T> src{nk};
+            wilson_hopping(L, U, src, site, col, hw);
+            src.get(site, col, own);
+        } else {
+            MemSource<S> src{reinterpret_cast<const S*>(a.in), nb};
+            wilson_hopping(L, U, src, site, col, hw);
+            src.get(site, col, own);
+        }
+        const size_t off = ((size_t)site * 12 * nb + col) * 2;
+        S* po = reinterpret_cast<S*>(a.out) + off;
+        cplx<T> out[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) {
+            out[e] = mul(ca, own[e]) + mul(cc, hw[e]);
+            st(po + (size_t)e * nb * 2, out[e]);
+        }
+        if (YMODE == 1) {
+            S* py = reinterpret_cast<S*>(a.y) + off;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) st(py + (size_t)e * nb * 2, mul(cya, own[e]) + mul(cyb, out[e]));
+        } else if (YMODE == 2) {
+            S* py = reinterpret_cast<S*>(a.y) + off;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) {
+                const cplx<T> yv = ld(py + (size_t)e * nb * 2);
+                st(py + (size_t)e * nb * 2, yv + mul(cyb, out[e]));
+            }
+        }
+        if (DOT) {
+            const uint32_t w = z4_word(nk, site, col);
+#pragma unroll
+            for (int e = 0; e < 12; ++e) dsum = dsum + z4_conj_mul<T>(w >> (2 * e), out[e]);
+        }
+    }
+    if (DOT) cta_dot_accumulate(dsum, col, colok, nb, a.dot_w, a.acc);
+}
+
+// ------------------------------------------------------------------ outer
+template <class S, bool DOT>
+__global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
+                                               int nb, NoiseKey nk, int sl) {
+    using T = typename Math<S>::T;
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool colok = col < nb;
+    const cplx<T> ca = cdv<T>(a.a), cc = cdv<T>(a.c), cb = cdv<T>(a.beta), cg = cdv<T>(a.gamma);
+    const cplx<T> c1b = {T(1.0 - a.beta[0]), T(-a.beta[1])};
+    cplx<T> dsum = cz<T>();
+    const int base = blockIdx.x * blockDim.y * sl;
+    for (int it = 0; it < sl; ++it) {
+        const int site = base + it * blockDim.y + threadIdx.y;
+        if (site >= L.V || !colok) continue;
+        cplx<T> hw[12], own[12];
+        MemSource<S> src{reinterpret_cast<const S*>(a.in), nb};
+        wilson_hopping(L, U, src, site, col, hw);
+        src.get(site, col, own);
+        const size_t off = ((size_t)site * 12 * nb + col) * 2;
+        const S* pw = reinterpret_cast<const S*>(a.w) + off;
+        S* pwo = reinterpret_cast<S*>(a.wout) + off;
+        S* py = reinterpret_cast<S*>(a.y) + off;
+        uint32_t wq = 0;
+        if (DOT) wq = z4_word(nk, site, col);
+#pragma unroll
+        for (int e = 0; e < 12; ++e) {
+            const cplx<T> t = mul(ca, own[e]) + mul(cc, hw[e]);
+            const cplx<T> wn = mul(c1b, ld(pw + (size_t)e * nb * 2)) + mul(cb, t);
+            st(pwo + (size_t)e * nb * 2, wn);
+            const cplx<T> yn = ld(py + (size_t)e * nb * 2) + mul(cg, wn);
+            st(py + (size_t)e * nb * 2, yn);
+            if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), yn);
+        }
+    }
+    if (DOT) cta_dot_accumulate(dsum, col, colok, nb, a.dot_w, a.acc);
+}
+
+// ------------------------------------------------------------------ elementwise
+template <class S>
+__global__ void k_fill_noise(int V, int nb, NoiseKey nk, double sre, double sim, S* out) {
+    using T = typename Math<S>::T;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)V * nb) return;
+    const int site = (int)(idx / nb), col = (int)(idx % nb);
+    const uint32_t w = z4_word(nk, site, col);
+    const cplx<T> sc = {T(sre), T(sim)};
+    S* p = out + ((size_t)site * 12 * nb + col) * 2;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) st(p + (size_t)e * nb * 2, mul(sc, z4_value<T>(w >> (2 * e))));
+}
+
+__global__ void k_noise_f64(int V, NoiseKey nk, int cnt, int ld_, int c0, double* out) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)V * cnt) return;
+    const int site = (int)(idx / cnt), col = (int)(idx % cnt);
+    const uint32_t w = z4_word(nk, site, col);
+    double* p = out + ((size_t)site * 12 * ld_ + c0 + col) * 2;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+        const cplx<double> v = z4_value<double>(w >> (2 * e));
+        p[(size_t)e * ld_ * 2] = v.re;
+        p[(size_t)e * ld_ * 2 + 1] = v.im;
+    }
+}
+
+template <class S>
+__global__ void k_import(size_t nrow, const double* __restrict__ src, int ld_, int c0, int cnt, S* dst, int nb) {
+    using T = typename Math<S>::T;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrow * nb) return;
+    const size_t row = idx / nb;
+    const int col = (int)(idx % nb);
+    cplx<T> v = cz<T>();
+    if (col < cnt) {
+        const double* p = src + (row * ld_ + c0 + col) * 2;
+        v = {T(p[0]), T(p[1])};
+    }
+    st(dst + idx * 2, v);
+}
+
+template <class S>
+__global__ void k_export(size_t nrow, const S* __restrict__ src, int nb, double* dst, int ld_, int c0, int cnt) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrow * cnt) return;
+    const size_t row = idx / cnt;
+    const int col = (int)(idx % cnt);
+    const auto v = ld(src + (row * nb + col) * 2);
+    double* p = dst + (row * ld_ + c0 + col) * 2;
+    p[0] = (double)v.re;
+    p[1] = (double)v.im;
+}
+
+template <class S>
+__global__ void k_scale(size_t n, const S* __restrict__ in, double sre, double sim, S* out) {
+    using T = typename Math<S>::T;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const cplx<T> sc = {T(sre), T(sim)};
+    st(out + idx * 2, mul(sc, ld(in + idx * 2)));
+}
+
+template <class T>
+__global__ void k_links(int V, const double* __restrict__ src, T* dst) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu, i)
+    if (idx >= (size_t)V * 36) return;
+    const int i = (int)(idx % 9);
+    const int mu = (int)((idx / 9) % 4);
+    const size_t site = idx / 36;
+    const double* p = src + (((size_t)mu * V + site) * 9 + i) * 2;
+    dst[idx * 2] = (T)p[0];
+    dst[idx * 2 + 1] = (T)p[1];
+}
+
+template <class T>
+__global__ void k_convert(size_t n, const double* __restrict__ src, T* dst) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * n) return;
+    dst[idx] = (T)src[idx];
+}
+
+// ------------------------------------------------------------------ finalize
+__global__ void k_finalize(int ncta, int nb, int nvalid, const double2* __restrict__ acc_hi,
+                           const double2* __restrict__ acc_lo, double2 chi, double2 clo,
+                           const double2* __restrict__ dterm, double2* samples, double2* hi, double2* lo) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nvalid) return;
+    double2 h = chi, l = clo;
+    for (int b = 0; b < ncta; ++b) h = cadd(h, acc_hi[(size_t)b * nb + col]);
+    if (acc_lo)
+        for (int b = 0; b < ncta; ++b) l = cadd(l, acc_lo[(size_t)b * nb + col]);
+    double2 s = make_double2(h.x - l.x, h.y - l.y);
+    if (dterm) s = make_double2(s.x - dterm[col].x, s.y - dterm[col].y);
+    samples[col] = s;
+    if (hi) hi[col] = h;
+    if (lo) lo[col] = l;
+}
+
+// ------------------------------------------------------------------ deflation dots
+// CTA: 32 noise columns x 4 site lanes; KT eigenvectors per CTA.  Each
+// thread sums, over its sites, conj(z_i) * b separately over the upper
+// (spin 0, 1) and lower (spin 2, 3) half: G1 = up + low, G2 = up - low
+// (gamma5 = diag(1, 1, -1, -1)).
+constexpr int DEFL_KT = 8;
+
+template <class T>
+__global__ void __launch_bounds__(128) k_defl_dots(int V, int k, const T* __restrict__ Z, int nb, NoiseKey nk,
+                                                   double2* part, int nsplit) {
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int i0 = blockIdx.y * DEFL_KT;
+    const int split = blockIdx.z;
+    const int chunk = (V + nsplit - 1) / nsplit;
+    const int s0 = split * chunk, s1 = min(V, s0 + chunk);
+    cplx<T> up[DEFL_KT], lo[DEFL_KT];
+#pragma unroll
+    for (int q = 0; q < DEFL_KT; ++q) { up[q] = cz<T>(); lo[q] = cz<T>(); }
+    const bool colok = col < nb;
+    for (int site = s0 + threadIdx.y; site < s1 && colok; site += blockDim.y) {
+        const uint32_t w = z4_word(nk, site, col);
+#pragma unroll
+        for (int q = 0; q < DEFL_KT; ++q) {
+            const int i = i0 + q;
+            if (i >= k) break;
+            const T* zp = Z + ((size_t)i * V + site) * 24;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) {
+                const cplx<T> z = ld(zp + 2 * e);
+                // conj(z) * i^q
+                const cplx<T> t = mul(cplx<T>{z.re, -z.im}, z4_value<T>(w >> (2 * e)));
+                if (e < 6) up[q] = up[q] + t; else lo[q] = lo[q] + t;
+            }
+        }
+    }
+    __shared__ double2 red[128][2];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < DEFL_KT; ++q) {
+        red[tid][0] = make_double2((double)up[q].re, (double)up[q].im);
+        red[tid][1] = make_double2((double)lo[q].re, (double)lo[q].im);
+        __syncthreads();
+        if (threadIdx.y == 0 && colok && i0 + q < k) {
+            double2 u = make_double2(0, 0), l = make_double2(0, 0);
+            for (int yy = 0; yy < (int)blockDim.y; ++yy) {
+                u = cadd(u, red[yy * 32 + threadIdx.x][0]);
+                l = cadd(l, red[yy * 32 + threadIdx.x][1]);
+            }
+            double2* p = part + (((size_t)split * k + (i0 + q)) * nb + col) * 2;
+            p[0] = make_double2(u.x + l.x, u.y + l.y);
+            p[1] = make_double2(u.x - l.x, u.y - l.y);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_defl_sum(int k, int nb, int nsplit, const double2* __restrict__ part, double2* G1, double2* G2) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)k * nb) return;
+    double2 g1 = make_double2(0, 0), g2 = make_double2(0, 0);
+    for (int s = 0; s < nsplit; ++s) {
+        const double2* p = part + (((size_t)s * k) * nb + idx) * 2;
+        g1 = cadd(g1, p[0]);
+        g2 = cadd(g2, p[1]);
+    }
+    G1[idx] = g1;
+    G2[idx] = g2;
+}
+
+__global__ void k_defl_term(int k, int nb, const double2* __restrict__ coef, const int* __restrict__ pair,
+                            const double2* __restrict__ G1, const double2* __restrict__ G2, double2* term) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nb) return;
+    double2 s = make_double2(0, 0);
+    for (int i = 0; i < k; ++i) {
+        const double2 bz = conjd(G1[(size_t)i * nb + col]);           // b^H z_i
+        const double2 ub = G2[(size_t)pair[i] * nb + col];            // z_pair^H gamma5 b
+        s = cadd(s, cmuld(coef[i], cmuld(bz, ub)));
+    }
+    term[col] = s;
+}
+
+template <class T>
+__global__ void k_defl_norms(int V, int k, const T* __restrict__ Z, const int* __restrict__ pair, double2* d) {
+    // one CTA per i; fixed-order tree over the CTA
+    const int i = blockIdx.x;
+    const T* zi = Z + (size_t)i * V * 24;
+    const T* zp = Z + (size_t)pair[i] * V * 24;
+    double sr = 0, si = 0;
+    for (size_t p = threadIdx.x; p < (size_t)V * 12; p += blockDim.x) {
+        const double ar = zp[2 * p], ai = zp[2 * p + 1], br = zi[2 * p], bi = zi[2 * p + 1];
+        const double g = ((p % 12) < 6) ? 1.0 : -1.0;
+        sr += g * (ar * br + ai * bi);
+        si += g * (ar * bi - ai * br);
+    }
+    __shared__ double rr[256], ri[256];
+    rr[threadIdx.x] = sr;
+    ri[threadIdx.x] = si;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) { rr[threadIdx.x] += rr[threadIdx.x + w]; ri[threadIdx.x] += ri[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d[i] = make_double2(rr[0], ri[0]);
+}
+
+// ------------------------------------------------------------------ FP64 Krylov vectors
+constexpr int MDOT_THREADS = 256;
+
+__global__ void k_mdot_part(size_t n, int m, const double2* __restrict__ Vb, const double2* __restrict__ w,
+                            double2* part) {
+    __shared__ double2 red[MDOT_THREADS];
+    const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const size_t p0 = blockIdx.x * chunk, p1 = min(n, p0 + chunk);
+    for (int j = 0; j < m; ++j) {
+        const double2* v = Vb + (size_t)j * n;
+        double2 s = make_double2(0, 0);
+        for (size_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) s = cadd(s, cmuld(conjd(v[p]), w[p]));
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + h]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * m + j] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_mdot_sum(int nparts, int m, const double2* __restrict__ part, double2* h) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double2 s = make_double2(0, 0);
+    for (int b = 0; b < nparts; ++b) s = cadd(s, part[(size_t)b * m + j]);
+    h[j] = s;
+}
+
+__global__ void k_maxpy(size_t n, int m, const double2* __restrict__ Vb, const double2* __restrict__ h, double2* w) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double2 s = w[p];
+    for (int j = 0; j < m; ++j) {
+        const double2 t = cmuld(h[j], Vb[(size_t)j * n + p]);
+        s = make_double2(s.x - t.x, s.y - t.y);
+    }
+    w[p] = s;
+}
+
+__global__ void k_norm2_part(size_t n, const double2* __restrict__ w, double* part) {
+    __shared__ double red[MDOT_THREADS];
+    double s = 0;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        s += w[p].x * w[p].x + w[p].y * w[p].y;
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_scalar(int nparts, const double* __restrict__ part, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0;
+        for (int b = 0; b < nparts; ++b) s += part[b];
+        *out = s;
+    }
+}
+
+__global__ void k_normalize(size_t n, const double2* __restrict__ w, const double* __restrict__ nrm2, double2* dst) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double inv = 1.0 / sqrt(*nrm2);
+    dst[p] = make_double2(w[p].x * inv, w[p].y * inv);
+}
+
+__global__ void k_combine(size_t n, int m, const double2* __restrict__ Vb, const double2* __restrict__ Y, int k,
+                          double2* Z) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (p >= n) return;
+    double2 s = make_double2(0, 0);
+    for (int j = 0; j < m; ++j) s = cadd(s, cmuld(Vb[(size_t)j * n + p], Y[(size_t)j * k + i]));
+    Z[(size_t)i * n + p] = s;
+}
+
+inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ================================================================== host side
+LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl) {
+    LaunchCfg c;
+    c.bx = std::min(nb, bx_max);
+    c.by = std::max(1, 256 / c.bx);
+    c.sl = std::max(1, sl);
+    c.gx = (g.V + c.by * c.sl - 1) / (c.by * c.sl);   // site blocks (x: no 65535 limit)
+    c.gy = (nb + c.bx - 1) / c.bx;                     // column blocks
+    return c;
+}
+
+template <class S>
+static void step_dispatch(const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a,
+                          const LaunchCfg& c, cudaStream_t s) {
+    using T = typename Math<S>::T;
+    const dim3 grid(c.gx, c.gy), block(c.bx, c.by);
+    const Lattice L = make_lat(g);
+    const NoiseKey nk = make_key(ns);
+    const T* U = reinterpret_cast<const T*>(links);
+    const bool noise = (a.in == nullptr);
+#define MPMC_STEP(NI, D, Y) k_step<S, NI, D, Y><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl)
+    if (noise) {
+        if (a.dot) {
+            if (a.ymode == 0) MPMC_STEP(true, true, 0); else if (a.ymode == 1) MPMC_STEP(true, true, 1); else MPMC_STEP(true, true, 2);
+        } else {
+            if (a.ymode == 0) MPMC_STEP(true, false, 0); else if (a.ymode == 1) MPMC_STEP(true, false, 1); else MPMC_STEP(true, false, 2);
+        }
+    } else {
+        if (a.dot) {
+            if (a.ymode == 0) MPMC_STEP(false, true, 0); else if (a.ymode == 1) MPMC_STEP(false, true, 1); else MPMC_STEP(false, true, 2);
+        } else {
+            if (a.ymode == 0) MPMC_STEP(false, false, 0); else if (a.ymode == 1) MPMC_STEP(false, false, 1); else MPMC_STEP(false, false, 2);
+        }
+    }
+#undef MPMC_STEP
+}
+
+void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a,
+                 const LaunchCfg& c, cudaStream_t s) {
+    if (storage == ST_F64) step_dispatch<double>(g, links, nb, ns, a, c, s);
+    else if (storage == ST_F32) step_dispatch<float>(g, links, nb, ns, a, c, s);
+    else step_dispatch<__nv_bfloat16>(g, links, nb, ns, a, c, s);
+}
+
+template <class S>
+static void outer_dispatch(const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a,
+                           const LaunchCfg& c, cudaStream_t s) {
+    using T = typename Math<S>::T;
+    const dim3 grid(c.gx, c.gy), block(c.bx, c.by);
+    const Lattice L = make_lat(g);
+    const NoiseKey nk = make_key(ns);
+    const T* U = reinterpret_cast<const T*>(links);
+    if (a.dot) k_outer<S, true><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl);
+    else k_outer<S, false><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl);
+}
+
+void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a,
+                  const LaunchCfg& c, cudaStream_t s) {
+    if (storage == ST_F64) outer_dispatch<double>(g, links, nb, ns, a, c, s);
+    else if (storage == ST_F32) outer_dispatch<float>(g, links, nb, ns, a, c, s);
+    else outer_dispatch<__nv_bfloat16>(g, links, nb, ns, a, c, s);
+}
+
+void launch_fill_noise(int storage, const Geom& g, int nb, const NoiseSpec& ns, const double sc[2], void* out,
+                       cudaStream_t s) {
+    const size_t n = (size_t)g.V * nb;
+    const NoiseKey nk = make_key(ns);
+    if (storage == ST_F64) k_fill_noise<double><<<blocks_for(n, 256), 256, 0, s>>>(g.V, nb, nk, sc[0], sc[1], (double*)out);
+    else if (storage == ST_F32) k_fill_noise<float><<<blocks_for(n, 256), 256, 0, s>>>(g.V, nb, nk, sc[0], sc[1], (float*)out);
+    else k_fill_noise<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(g.V, nb, nk, sc[0], sc[1], (__nv_bfloat16*)out);
+}
+
+void launch_noise_f64(const Geom& g, const NoiseSpec& ns, int cnt, int ld_, int c0, double* out, cudaStream_t s) {
+    const size_t n = (size_t)g.V * cnt;
+    k_noise_f64<<<blocks_for(n, 256), 256, 0, s>>>(g.V, make_key(ns), cnt, ld_, c0, out);
+}
+
+void launch_import(int storage, int V, const double* src, int ld_, int c0, int cnt, void* dst, int nb,
+                   cudaStream_t s) {
+    const size_t nrow = (size_t)V * 12, n = nrow * nb;
+    if (storage == ST_F64) k_import<double><<<blocks_for(n, 256), 256, 0, s>>>(nrow, src, ld_, c0, cnt, (double*)dst, nb);
+    else if (storage == ST_F32) k_import<float><<<blocks_for(n, 256), 256, 0, s>>>(nrow, src, ld_, c0, cnt, (float*)dst, nb);
+    else k_import<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(nrow, src, ld_, c0, cnt, (__nv_bfloat16*)dst, nb);
+}
+
+void launch_export(int storage, int V, const void* src, int nb, double* dst, int ld_, int c0, int cnt,
+                   cudaStream_t s) {
+    const size_t nrow = (size_t)V * 12, n = nrow * cnt;
+    if (storage == ST_F64) k_export<double><<<blocks_for(n, 256), 256, 0, s>>>(nrow, (const double*)src, nb, dst, ld_, c0, cnt);
+    else if (storage == ST_F32) k_export<float><<<blocks_for(n, 256), 256, 0, s>>>(nrow, (const float*)src, nb, dst, ld_, c0, cnt);
+    else k_export<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(nrow, (const __nv_bfloat16*)src, nb, dst, ld_, c0, cnt);
+}
+
+void launch_scale(int storage, size_t n, const void* in, const double sc[2], void* out, cudaStream_t s) {
+    if (storage == ST_F64) k_scale<double><<<blocks_for(n, 256), 256, 0, s>>>(n, (const double*)in, sc[0], sc[1], (double*)out);
+    else if (storage == ST_F32) k_scale<float><<<blocks_for(n, 256), 256, 0, s>>>(n, (const float*)in, sc[0], sc[1], (float*)out);
+    else k_scale<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(n, (const __nv_bfloat16*)in, sc[0], sc[1], (__nv_bfloat16*)out);
+}
+
+void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s) {
+    const size_t n = (size_t)V * 36;
+    if (storage == ST_F64) k_links<double><<<blocks_for(n, 256), 256, 0, s>>>(V, src, (double*)dst);
+    else k_links<float><<<blocks_for(n, 256), 256, 0, s>>>(V, src, (float*)dst);
+}
+
+void launch_convert_vectors(int storage, size_t ncplx, const double* src, void* dst, cudaStream_t s) {
+    if (storage == ST_F64) k_convert<double><<<blocks_for(2 * ncplx, 256), 256, 0, s>>>(ncplx, src, (double*)dst);
+    else k_convert<float><<<blocks_for(2 * ncplx, 256), 256, 0, s>>>(ncplx, src, (float*)dst);
+}
+
+void launch_finalize(int ncta, int nb, int nvalid, const double2* acc_hi, const double2* acc_lo, const double c_hi[2],
+                     const double c_lo[2], const double2* dterm, double2* samples, double2* hi, double2* lo,
+                     cudaStream_t s) {
+    k_finalize<<<blocks_for(nvalid, 128), 128, 0, s>>>(ncta, nb, nvalid, acc_hi, acc_lo, make_double2(c_hi[0], c_hi[1]),
+                                                      make_double2(c_lo[0], c_lo[1]), dterm, samples, hi, lo);
+}
+
+int defl_nsplit(int V) { return std::max(1, std::min(64, V / 128)); }
+
+void launch_defl_dots(int storage, const Geom& g, int k, const void* Z, int nb, const NoiseSpec& ns, double2* part,
+                      int nsplit, cudaStream_t s) {
+    const dim3 grid((nb + 31) / 32, (k + DEFL_KT - 1) / DEFL_KT, nsplit), block(32, 4);
+    if (storage == ST_F64) k_defl_dots<double><<<grid, block, 0, s>>>(g.V, k, (const double*)Z, nb, make_key(ns), part, nsplit);
+    else k_defl_dots<float><<<grid, block, 0, s>>>(g.V, k, (const float*)Z, nb, make_key(ns), part, nsplit);
+}
+
+void launch_defl_reduce(int k, int nb, int nsplit, const double2* part, const double2* coef, const int* pair,
+                        double2* G1, double2* G2, double2* term, cudaStream_t s) {
+    const size_t n = (size_t)k * nb;
+    k_defl_sum<<<blocks_for(n, 256), 256, 0, s>>>(k, nb, nsplit, part, G1, G2);
+    k_defl_term<<<blocks_for(nb, 128), 128, 0, s>>>(k, nb, coef, pair, G1, G2, term);
+}
+
+void launch_defl_norms(int storage, int V, int k, const void* Z, const int* pair, double2* d, cudaStream_t s) {
+    if (storage == ST_F64) k_defl_norms<double><<<k, 256, 0, s>>>(V, k, (const double*)Z, pair, d);
+    else k_defl_norms<float><<<k, 256, 0, s>>>(V, k, (const float*)Z, pair, d);
+}
+
+int mdot_parts(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>(304, n / 1024)); }
+
+void launch_mdot(size_t n, int m, const double2* Vb, const double2* w, double2* part, double2* h, cudaStream_t s) {
+    const int np = mdot_parts(n);
+    k_mdot_part<<<np, MDOT_THREADS, 0, s>>>(n, m, Vb, w, part);
+    k_mdot_sum<<<blocks_for(m, 128), 128, 0, s>>>(np, m, part, h);
+}
+
+void launch_maxpy(size_t n, int m, const double2* Vb, const double2* h, double2* w, cudaStream_t s) {
+    k_maxpy<<<blocks_for(n, 256), 256, 0, s>>>(n, m, Vb, h, w);
+}
+
+void launch_norm2(size_t n, const double2* w, double* part, double* out, cudaStream_t s) {
+    const int np = mdot_parts(n);
+    k_norm2_part<<<np, MDOT_THREADS, 0, s>>>(n, w, part);
+    k_sum_scalar<<<1, 32, 0, s>>>(np, part, out);
+}
+
+void launch_normalize(size_t n, const double2* w, const double* nrm2, double2* dst, cudaStream_t s) {
+    k_normalize<<<blocks_for(n, 256), 256, 0, s>>>(n, w, nrm2, dst);
+}
+
+void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k, double2* Z, cudaStream_t s) {
+    const dim3 grid(blocks_for(n, 256), k);
+    k_combine<<<grid, 256, 0, s>>>(n, m, Vb, Y, k, Z);
+}
+
+}  // namespace mpmc

@@ -1,0 +1,115 @@
+// Host-side launch interface of the CUDA kernels (no templates, no torch).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpmc {
+
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };
+
+struct Geom {
+    int lx, ly, lz, lt, V, bc_t;
+};
+
+struct NoiseSpec {
+    uint64_t seed;
+    uint32_t level;
+    uint32_t j0;
+};
+
+// One degree step of the root form (Sec. 2.3):
+//   out = a * in + c * H in      (a = 1 - 1/theta, c = kappa/theta, i.e. out = in - A in / theta)
+// optional:  y = ya * in + yb * out (ymode 1)  or  y += yb * out (ymode 2)
+// optional:  acc[cta][col] += dot_w * sum_sites b^H out   (b = the column's Z4 noise)
+// in == nullptr means "in is the noise block itself".
+struct StepArgs {
+    const void* in;
+    void* out;
+    void* y;
+    int ymode;
+    bool dot;
+    double a[2], c[2], ya[2], yb[2];
+    double dot_w[2];
+    double2* acc;
+};
+
+// Last inner step of a composite outer step (Sec. 3.2):
+//   t  = a * in + c * H in                    (t = pi_in(A) w, not stored)
+//   wn = (1 - beta) * w + beta * t            (wn = (I - B/eta) w, B = A p_in(A))
+//   y += gamma * wn;  optional acc += dot_w * b^H y
+struct OuterArgs {
+    const void* in;
+    const void* w;
+    void* wout;
+    void* y;
+    double a[2], c[2], beta[2], gamma[2];
+    bool dot;
+    double dot_w[2];
+    double2* acc;
+};
+
+struct LaunchCfg {
+    int bx, by, sl, gx, gy;   // block (bx, by), site loop sl, grid (gx, gy)
+};
+
+LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl);
+
+void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
+                 const StepArgs& a, const LaunchCfg& cfg, cudaStream_t s);
+void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
+                  const OuterArgs& a, const LaunchCfg& cfg, cudaStream_t s);
+
+// out = scale * noise block (all nb columns)
+void launch_fill_noise(int storage, const Geom& g, int nb, const NoiseSpec& ns, const double scale[2],
+                       void* out, cudaStream_t s);
+// noise block as complex double in the C-ABI layout [site][e][ld] columns c0..c0+cnt
+void launch_noise_f64(const Geom& g, const NoiseSpec& ns, int cnt, int ld, int c0, double* out, cudaStream_t s);
+// dst (storage, [site][e][nb]) = src columns c0..c0+cnt of a complex-double [site][e][ld] block; zero pad
+void launch_import(int storage, int V, const double* src, int ld, int c0, int cnt, void* dst, int nb,
+                   cudaStream_t s);
+// dst columns c0..c0+cnt of complex-double [site][e][ld] = src (storage) columns 0..cnt
+void launch_export(int storage, int V, const void* src, int nb, double* dst, int ld, int c0, int cnt,
+                   cudaStream_t s);
+// out = s * in (storage buffers of V*12*nb complex)
+void launch_scale(int storage, size_t ncplx, const void* in, const double sc[2], void* out, cudaStream_t s);
+// links: complex double [mu][site][3][3] -> math precision [site][mu][3][3]
+void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s);
+
+// samples[j0 + col] = sum_cta acc_hi + const_hi - (sum_cta acc_lo + const_lo) - dterm[col]
+// also hi/lo parts (may be null).  acc_lo/dterm may be null.
+void launch_finalize(int ncta, int nb, int nvalid, const double2* acc_hi, const double2* acc_lo,
+                     const double c_hi[2], const double c_lo[2], const double2* dterm,
+                     double2* samples, double2* hi, double2* lo, cudaStream_t s);
+
+// Deflation dots of Sec. 4.1 for a noise block:
+//   G1[i][col] = z_i^H b_col,  G2[i][col] = z_i^H gamma5 b_col
+// Z: math precision, k vectors of V*12 complex.  part: scratch [nsplit][k][nb][2] double2.
+int defl_nsplit(int V);
+void launch_defl_dots(int storage, const Geom& g, int k, const void* Z, int nb, const NoiseSpec& ns,
+                      double2* part, int nsplit, cudaStream_t s);
+// term[col] = sum_i coef[i] * conj(G1[i][col]) * G2[pair[i]][col]; G1, G2 written too (k x nb each)
+void launch_defl_reduce(int k, int nb, int nsplit, const double2* part, const double2* coef, const int* pair,
+                        double2* G1, double2* G2, double2* term, cudaStream_t s);
+// d[i] = z_pair[i]^H gamma5 z_i (FP64 accumulation of the stored vectors)
+void launch_defl_norms(int storage, int V, int k, const void* Z, const int* pair, double2* d, cudaStream_t s);
+// Z (math precision) from complex double host-layout vectors
+void launch_convert_vectors(int storage, size_t ncplx, const double* src, void* dst, cudaStream_t s);
+
+// FP64 Krylov helpers on complex-double vectors of n complex
+// h[j] = V_j^H w for j < m (two-level fixed-order reduction through part)
+void launch_mdot(size_t n, int m, const double2* Vb, const double2* w, double2* part, double2* h,
+                 cudaStream_t s);
+// w -= sum_j h[j] V_j
+void launch_maxpy(size_t n, int m, const double2* Vb, const double2* h, double2* w, cudaStream_t s);
+// out[0] = ||w||^2
+void launch_norm2(size_t n, const double2* w, double* part, double* out, cudaStream_t s);
+// dst = w * (1/nrm)   where *nrm2 is ||w||^2 on the device
+void launch_normalize(size_t n, const double2* w, const double* nrm2, double2* dst, cudaStream_t s);
+// Z_i = sum_j V_j Y[j][i]
+void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k, double2* Z, cudaStream_t s);
+// complex double [site][e][1] <-> storage conversions for a single vector are import/export with nb = 1
+
+int mdot_parts(size_t n);
+
+}  // namespace mpmc

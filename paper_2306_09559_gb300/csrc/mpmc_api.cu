@@ -1,0 +1,1005 @@
+// Host runtime of the C ABI declared in include/mpmc.h: handle lifetime,
+// polynomial chains (root form, composite, projected composite), the level
+// engine of the multilevel Monte Carlo and the FP64 Arnoldi setup.
+#include "mpmc.h"
+#include "kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using cd = std::complex<double>;
+using namespace mpmc;
+
+namespace {
+
+struct PolyDef {
+    bool set = false;
+    int kind = MPMC_SINGLE;
+    std::vector<cd> roots, outer;   // theta (single / inner), eta (outer)
+};
+
+// Device work buffers for one storage format and block width.
+struct Workspace {
+    int storage = -1;
+    int nb = 0;
+    int V = 0;
+    void* w[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* y = nullptr;
+    void* r = nullptr;        // imported input block / start vectors
+    void* x = nullptr;        // output block of apply_poly
+    double2* acc_hi = nullptr;
+    double2* acc_lo = nullptr;
+    int acc_rows = 0;
+    LaunchCfg cfg{};
+};
+
+size_t storage_bytes(int st) { return st == ST_F64 ? 16 : (st == ST_F32 ? 8 : 4); }
+
+}  // namespace
+
+struct mpmc_ctx {
+    Geom g{};
+    double kappa = 0;
+    int prec = MPMC_FP64;
+    int storage = ST_F64;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    void* links64 = nullptr;      // [site][mu][3][3] complex double
+    void* links32 = nullptr;      // same in float (FP32 / BF16S handles)
+    PolyDef polys[MPMC_MAX_POLYS];
+    // deflation
+    int k = 0;
+    void* Z = nullptr;            // k vectors in the math precision (double or float)
+    int* d_pair = nullptr;
+    std::vector<cd> lam;
+    std::vector<int> pair;
+    std::vector<cd> dnorm;        // d_i = z_pair(i)^H gamma5 z_i of the stored vectors
+    double2* d_dnorm = nullptr;
+    double2* d_coef = nullptr;    // [MPMC_MAX_POLYS][k] c_i / d_i per level
+    void* AZ = nullptr;           // A z_i, math precision (projected composite)
+    double2* d_Hinv = nullptr;    // (U^H A Z)^{-1}, k x k row-major
+    double2* defl_part = nullptr;
+    double2* G1 = nullptr;
+    double2* G2 = nullptr;
+    double2* dterm = nullptr;
+    double2* D = nullptr;         // projection coefficients k x nb
+    double2* xz = nullptr;        // b^H Z D per column
+    int defl_nb = 0;
+    // work
+    int nb_user = 0;
+    Workspace ws, ws64;
+    double2* samples = nullptr;
+    size_t samples_cap = 0;
+    double* io = nullptr;         // complex-double staging for host I/O
+    size_t io_cap = 0;
+    double2* kr_part = nullptr;   // Krylov scratch
+    double2* kr_h = nullptr;
+    double* kr_nrm = nullptr;
+    int kr_m = 0;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(mpmc_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_check(mpmc_ctx* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MPMC_OK;
+    return fail(h, e == cudaErrorMemoryAllocation ? MPMC_ENOMEM : MPMC_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        int rc__ = cuda_check(h, (call), #call);              \
+        if (rc__) return rc__;                                \
+    } while (0)
+
+#define LAUNCHED(n)                                                    \
+    do {                                                               \
+        h->launches += (n);                                            \
+        int rc__ = cuda_check(h, cudaGetLastError(), "kernel launch"); \
+        if (rc__) return rc__;                                         \
+    } while (0)
+
+template <class P> int dev_alloc(mpmc_ctx* h, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(h, MPMC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+    }
+    *p = reinterpret_cast<P*>(q);
+    return MPMC_OK;
+}
+
+template <class P> void dev_free(P*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+bool finite(cd z) { return std::isfinite(z.real()) && std::isfinite(z.imag()); }
+
+int nsites12(const mpmc_ctx* h) { return 12 * h->g.V; }
+
+void free_ws(Workspace& w) {
+    for (auto& p : w.w) dev_free(p);
+    dev_free(w.y);
+    dev_free(w.r);
+    dev_free(w.x);
+    dev_free(w.acc_hi);
+    dev_free(w.acc_lo);
+    w.nb = 0;
+    w.storage = -1;
+}
+
+int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
+    if (w.storage == storage && w.nb == nb) return MPMC_OK;
+    free_ws(w);
+    const size_t vb = (size_t)h->g.V * 12 * nb * storage_bytes(storage);
+    for (auto& p : w.w)
+        if (int rc = dev_alloc(h, &p, vb)) return rc;
+    if (int rc = dev_alloc(h, &w.y, vb)) return rc;
+    if (int rc = dev_alloc(h, &w.r, vb)) return rc;
+    if (int rc = dev_alloc(h, &w.x, vb)) return rc;
+    w.cfg = chain_config(h->g, nb, 64, 1);
+    w.acc_rows = w.cfg.gx;   // one accumulator row per site block
+    if (int rc = dev_alloc(h, &w.acc_hi, sizeof(double2) * (size_t)w.acc_rows * nb)) return rc;
+    if (int rc = dev_alloc(h, &w.acc_lo, sizeof(double2) * (size_t)w.acc_rows * nb)) return rc;
+    // padding columns must hold finite values: clear everything once
+    for (auto& p : w.w) CK(cudaMemsetAsync(p, 0, vb, h->stream));
+    CK(cudaMemsetAsync(w.y, 0, vb, h->stream));
+    CK(cudaMemsetAsync(w.r, 0, vb, h->stream));
+    CK(cudaMemsetAsync(w.x, 0, vb, h->stream));
+    w.storage = storage;
+    w.nb = nb;
+    w.V = h->g.V;
+    return MPMC_OK;
+}
+
+const void* links_for(const mpmc_ctx* h, int storage) { return storage == ST_F64 ? h->links64 : h->links32; }
+
+// ------------------------------------------------------------------ roots
+std::vector<int> leja_order(const std::vector<cd>& r) {
+    const int m = (int)r.size();
+    std::vector<int> order;
+    if (m == 0) return order;
+    std::vector<char> taken(m, 0);
+    std::vector<double> score(m, 0.0);
+    int first = 0;
+    for (int i = 1; i < m; ++i)
+        if (std::abs(r[i]) > std::abs(r[first])) first = i;
+    order.push_back(first);
+    taken[first] = 1;
+    for (int step = 1; step < m; ++step) {
+        const cd last = r[order.back()];
+        int best = -1;
+        double bs = -INFINITY;
+        for (int i = 0; i < m; ++i) {
+            if (taken[i]) continue;
+            const double d = std::abs(r[i] - last);
+            score[i] += (d > 0) ? std::log(d) : -INFINITY;
+            if (best < 0 || score[i] > bs) { best = i; bs = score[i]; }
+        }
+        order.push_back(best);
+        taken[best] = 1;
+    }
+    return order;
+}
+
+// p(lambda) in root form: sum_i theta_i^{-1} prod_{j<i} (1 - lambda/theta_j)
+cd poly_value(const std::vector<cd>& th, cd lam) {
+    cd w = 1.0, y = 0.0;
+    for (size_t i = 0; i < th.size(); ++i) {
+        y += w / th[i];
+        w *= (1.0 - lam / th[i]);
+    }
+    return y;
+}
+
+cd spec_value(const PolyDef& p, cd lam) {
+    if (p.kind == MPMC_SINGLE) return poly_value(p.roots, lam);
+    if (p.kind == MPMC_COMPOSITE) {
+        const cd pin = poly_value(p.roots, lam);
+        return pin * poly_value(p.outer, lam * pin);
+    }
+    return 1.0 / lam;   // projected composite maps z_i to z_i / lambda_i
+}
+
+long long spec_matvecs(const PolyDef& p) {
+    const long long m = (long long)p.roots.size();
+    if (p.kind == MPMC_SINGLE) return std::max(0LL, m - 1);
+    const long long mo = (long long)p.outer.size();
+    return (mo - 1) * m + (m - 1);
+}
+
+int num_levels(const mpmc_ctx* h) {
+    int L = 0;
+    while (L < MPMC_MAX_POLYS && h->polys[L].set) ++L;
+    return L;
+}
+
+inline void setc(double (&d)[2], cd z) { d[0] = z.real(); d[1] = z.imag(); }
+
+// ------------------------------------------------------------------ chains
+// Trace mode: acc += sum of weighted b^H w over all steps of p(A) applied to
+// the start block (noise when start == nullptr); *cst receives the weighted
+// b^H w_0 term known in closed form (b^H b = 12 V for noise starts).
+int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& ns, const void* start,
+                double2* acc, cd* cst) {
+    const int st = ws.storage, nb = ws.nb;
+    const void* U = links_for(h, st);
+    const double n = (double)nsites12(h);
+    const LaunchCfg& cfg = ws.cfg;
+    CK(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)ws.acc_rows * nb, h->stream));
+    *cst = 0.0;
+    auto single_from = [&](const std::vector<cd>& th, const void* in0, bool in_is_noise_start) -> int {
+        // steps j = 1..m-1 produce w_j with dot weight 1/theta_{j+1}
+        const int m = (int)th.size();
+        const void* in = in0;
+        for (int j = 1; j < m; ++j) {
+            StepArgs a{};
+            a.in = (j == 1 && in_is_noise_start) ? nullptr : in;
+            a.out = ws.w[(j - 1) % 2];
+            a.y = nullptr;
+            a.ymode = 0;
+            a.dot = true;
+            const cd al = 1.0 / th[j - 1];
+            setc(a.a, 1.0 - al);
+            setc(a.c, h->kappa * al);
+            setc(a.dot_w, 1.0 / th[j]);
+            a.acc = acc;
+            launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
+            LAUNCHED(1);
+            in = a.out;
+        }
+        return MPMC_OK;
+    };
+    if (p.kind == MPMC_SINGLE) {
+        if (start == nullptr) *cst = n / p.roots[0];
+        else return fail(h, MPMC_EINVAL, "internal: single chain from a buffer in trace mode");
+        return single_from(p.roots, nullptr, true);
+    }
+    // composite: outer root form on B = A p_in(A) = I - pi_in(A), then p_in(A) y
+    const std::vector<cd>& th = p.roots;
+    const std::vector<cd>& eta = p.outer;
+    const int m_in = (int)th.size(), m_out = (int)eta.size();
+    const size_t ncplx = (size_t)h->g.V * 12 * nb;
+    void* Wcur;
+    void* Wnxt;
+    if (start == nullptr) {
+        double one[2] = {1.0, 0.0};
+        launch_fill_noise(st, h->g, nb, ns, one, ws.w[2], h->stream);
+        LAUNCHED(1);
+        Wcur = ws.w[2];
+    } else {
+        Wcur = const_cast<void*>(start);
+    }
+    Wnxt = ws.w[3];
+    {
+        double s1[2];
+        setc(s1, 1.0 / eta[0]);
+        launch_scale(st, ncplx, Wcur, s1, ws.y, h->stream);
+        LAUNCHED(1);
+    }
+    if (m_out == 1) {
+        // y = b / eta_1; the final chain's first dot is in closed form only for noise starts
+        if (start == nullptr) *cst = n / (eta[0] * th[0]);
+        else return fail(h, MPMC_ENOTSUP, "internal: projected composite needs at least two outer roots");
+    }
+    for (int k = 1; k < m_out; ++k) {
+        const void* in = Wcur;
+        for (int j = 1; j < m_in; ++j) {
+            StepArgs a{};
+            a.in = in;
+            a.out = ws.w[(j - 1) % 2];
+            a.ymode = 0;
+            a.dot = false;
+            const cd al = 1.0 / th[j - 1];
+            setc(a.a, 1.0 - al);
+            setc(a.c, h->kappa * al);
+            launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
+            LAUNCHED(1);
+            in = a.out;
+        }
+        OuterArgs o{};
+        o.in = in;
+        o.w = Wcur;
+        o.wout = Wnxt;
+        o.y = ws.y;
+        const cd al = 1.0 / th[m_in - 1];
+        setc(o.a, 1.0 - al);
+        setc(o.c, h->kappa * al);
+        setc(o.beta, 1.0 / eta[k - 1]);
+        setc(o.gamma, 1.0 / eta[k]);
+        o.dot = (k == m_out - 1);
+        setc(o.dot_w, 1.0 / th[0]);
+        o.acc = acc;
+        launch_outer(st, h->g, U, nb, ns, o, cfg, h->stream);
+        LAUNCHED(1);
+        // never write into the caller's start buffer: alternate between w[2] and w[3]
+        Wcur = Wnxt;
+        Wnxt = (Wcur == ws.w[3]) ? ws.w[2] : ws.w[3];
+    }
+    // final chain x = p_in(A) y with dots; steps j = 1..m_in-1
+    const void* in = ws.y;
+    for (int j = 1; j < m_in; ++j) {
+        StepArgs a{};
+        a.in = in;
+        a.out = ws.w[(j - 1) % 2];
+        a.ymode = 0;
+        a.dot = true;
+        const cd al = 1.0 / th[j - 1];
+        setc(a.a, 1.0 - al);
+        setc(a.c, h->kappa * al);
+        setc(a.dot_w, 1.0 / th[j]);
+        a.acc = acc;
+        launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
+        LAUNCHED(1);
+        in = a.out;
+    }
+    return MPMC_OK;
+}
+
+// Apply mode: X = p(A) B for the block in `in` (storage of ws); X must not alias ws buffers.
+int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, const void* in0, void* X) {
+    const int st = ws.storage, nb = ws.nb;
+    const void* U = links_for(h, st);
+    const NoiseSpec ns{0, 0, 0};
+    const int m = (int)th.size();
+    const size_t ncplx = (size_t)h->g.V * 12 * nb;
+    if (m == 1) {
+        double s1[2];
+        setc(s1, 1.0 / th[0]);
+        launch_scale(st, ncplx, in0, s1, X, h->stream);
+        LAUNCHED(1);
+        return MPMC_OK;
+    }
+    const void* in = in0;
+    for (int j = 1; j < m; ++j) {
+        StepArgs a{};
+        a.in = in;
+        a.out = ws.w[(j - 1) % 2];
+        a.y = X;
+        a.ymode = (j == 1) ? 1 : 2;
+        a.dot = false;
+        const cd al = 1.0 / th[j - 1];
+        setc(a.a, 1.0 - al);
+        setc(a.c, h->kappa * al);
+        setc(a.ya, 1.0 / th[0]);
+        setc(a.yb, 1.0 / th[j]);
+        launch_step(st, h->g, U, nb, ns, a, ws.cfg, h->stream);
+        LAUNCHED(1);
+        in = a.out;
+    }
+    return MPMC_OK;
+}
+
+int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, void* X) {
+    if (p.kind == MPMC_SINGLE) return chain_apply_single(h, ws, p.roots, in0, X);
+    const int st = ws.storage, nb = ws.nb;
+    const void* U = links_for(h, st);
+    const NoiseSpec ns{0, 0, 0};
+    const std::vector<cd>& th = p.roots;
+    const std::vector<cd>& eta = p.outer;
+    const int m_in = (int)th.size(), m_out = (int)eta.size();
+    const size_t ncplx = (size_t)h->g.V * 12 * nb;
+    double s1[2];
+    setc(s1, 1.0 / eta[0]);
+    launch_scale(st, ncplx, in0, s1, ws.y, h->stream);
+    LAUNCHED(1);
+    const void* Wcur = in0;
+    void* Wnxt = ws.w[2];
+    for (int k = 1; k < m_out; ++k) {
+        const void* in = Wcur;
+        for (int j = 1; j < m_in; ++j) {
+            StepArgs a{};
+            a.in = in;
+            a.out = ws.w[(j - 1) % 2];
+            const cd al = 1.0 / th[j - 1];
+            setc(a.a, 1.0 - al);
+            setc(a.c, h->kappa * al);
+            launch_step(st, h->g, U, nb, ns, a, ws.cfg, h->stream);
+            LAUNCHED(1);
+            in = a.out;
+        }
+        OuterArgs o{};
+        o.in = in;
+        o.w = Wcur;
+        o.wout = Wnxt;
+        o.y = ws.y;
+        const cd al = 1.0 / th[m_in - 1];
+        setc(o.a, 1.0 - al);
+        setc(o.c, h->kappa * al);
+        setc(o.beta, 1.0 / eta[k - 1]);
+        setc(o.gamma, 1.0 / eta[k]);
+        o.dot = false;
+        launch_outer(st, h->g, U, nb, ns, o, ws.cfg, h->stream);
+        LAUNCHED(1);
+        Wcur = Wnxt;
+        Wnxt = (Wcur == ws.w[2]) ? ws.w[3] : ws.w[2];
+    }
+    // x = p_in(A) y; y lives in ws.y which chain_apply_single does not touch
+    return chain_apply_single(h, ws, th, ws.y, X);
+}
+
+int apply_A(mpmc_ctx* h, Workspace& ws, const void* in, void* out) {
+    StepArgs a{};
+    a.in = in;
+    a.out = out;
+    setc(a.a, 1.0);
+    setc(a.c, -h->kappa);
+    const NoiseSpec ns{0, 0, 0};
+    launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
+    LAUNCHED(1);
+    return MPMC_OK;
+}
+
+int default_nb(const mpmc_ctx* h) {
+    if (h->nb_user > 0) return h->nb_user;
+    // keep the six work vectors within ~24 GB
+    const size_t per = (size_t)h->g.V * 12 * storage_bytes(h->storage) * 6;
+    int nb = 64;
+    while (nb > 1 && per * nb > (size_t)24 << 30) nb /= 2;
+    return nb;
+}
+
+int ensure_io(mpmc_ctx* h, size_t ncplx) {
+    if (h->io_cap >= ncplx) return MPMC_OK;
+    dev_free(h->io);
+    h->io_cap = 0;
+    if (int rc = dev_alloc(h, &h->io, ncplx * 16)) return rc;
+    h->io_cap = ncplx;
+    return MPMC_OK;
+}
+
+int ensure_defl_work(mpmc_ctx* h, int nb) {
+    if (h->k == 0) return MPMC_OK;
+    if (h->defl_nb == nb) return MPMC_OK;
+    dev_free(h->defl_part);
+    dev_free(h->G1);
+    dev_free(h->G2);
+    dev_free(h->dterm);
+    dev_free(h->D);
+    dev_free(h->xz);
+    const int ns = defl_nsplit(h->g.V);
+    if (int rc = dev_alloc(h, &h->defl_part, sizeof(double2) * 2 * (size_t)ns * h->k * nb)) return rc;
+    if (int rc = dev_alloc(h, &h->G1, sizeof(double2) * (size_t)h->k * nb)) return rc;
+    if (int rc = dev_alloc(h, &h->G2, sizeof(double2) * (size_t)h->k * nb)) return rc;
+    if (int rc = dev_alloc(h, &h->dterm, sizeof(double2) * nb)) return rc;
+    if (int rc = dev_alloc(h, &h->D, sizeof(double2) * (size_t)h->k * nb)) return rc;
+    if (int rc = dev_alloc(h, &h->xz, sizeof(double2) * nb)) return rc;
+    h->defl_nb = nb;
+    return MPMC_OK;
+}
+
+int level_coefficients(mpmc_ctx* h, int level, std::vector<cd>& c) {
+    const int L = num_levels(h);
+    c.assign(h->k, 0.0);
+    if (h->k == 0 || level >= L - 1) return MPMC_OK;
+    for (int i = 0; i < h->k; ++i) {
+        c[i] = spec_value(h->polys[level], h->lam[i]) - spec_value(h->polys[level + 1], h->lam[i]);
+        if (!finite(c[i])) return fail(h, MPMC_ENONFINITE, "non-finite deflation coefficient");
+    }
+    return MPMC_OK;
+}
+
+void free_deflation(mpmc_ctx* h) {
+    dev_free(h->Z);
+    dev_free(h->d_pair);
+    dev_free(h->d_dnorm);
+    dev_free(h->d_coef);
+    dev_free(h->AZ);
+    dev_free(h->d_Hinv);
+    dev_free(h->defl_part);
+    dev_free(h->G1);
+    dev_free(h->G2);
+    dev_free(h->dterm);
+    dev_free(h->D);
+    dev_free(h->xz);
+    h->defl_nb = 0;
+    h->k = 0;
+    h->lam.clear();
+    h->pair.clear();
+    h->dnorm.clear();
+}
+
+int upload_coefficients(mpmc_ctx* h) {
+    if (h->k == 0) return MPMC_OK;
+    std::vector<double2> all((size_t)MPMC_MAX_POLYS * h->k, make_double2(0, 0));
+    const int L = num_levels(h);
+    for (int l = 0; l + 1 < L; ++l) {
+        std::vector<cd> c;
+        if (int rc = level_coefficients(h, l, c)) return rc;
+        for (int i = 0; i < h->k; ++i) {
+            const cd q = c[i] / h->dnorm[i];
+            all[(size_t)l * h->k + i] = make_double2(q.real(), q.imag());
+        }
+    }
+    CK(cudaMemcpyAsync(h->d_coef, all.data(), sizeof(double2) * all.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPMC_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+const char* mpmc_strerror(int code) {
+    switch (code) {
+        case MPMC_OK: return "ok";
+        case MPMC_EINVAL: return "invalid argument";
+        case MPMC_ENOMEM: return "out of memory";
+        case MPMC_ENOTSUP: return "not supported";
+        case MPMC_ETIMEOUT: return "device wait timed out";
+        case MPMC_ENONFINITE: return "non-finite value";
+        case MPMC_ECUDA: return "CUDA error";
+        case MPMC_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+const char* mpmc_last_error(mpmc_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+long long mpmc_launch_count(mpmc_handle h) { return h ? h->launches : 0; }
+
+int mpmc_create(mpmc_handle* out, const int dims[4], const double* links, double kappa, int precision, int bc_t) {
+    if (!out) return MPMC_EINVAL;
+    *out = nullptr;
+    if (!dims || !links) return MPMC_EINVAL;
+    for (int d = 0; d < 4; ++d)
+        if (dims[d] < 2 || dims[d] > 4096) return MPMC_EINVAL;
+    if (!std::isfinite(kappa)) return MPMC_EINVAL;
+    if (bc_t != 1 && bc_t != -1) return MPMC_EINVAL;
+    if (precision != MPMC_FP64 && precision != MPMC_FP32 && precision != MPMC_BF16S) return MPMC_ENOTSUP;
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V * 12 > (1LL << 31) - 1) return MPMC_EINVAL;
+    mpmc_ctx* h = new (std::nothrow) mpmc_ctx();
+    if (!h) return MPMC_ENOMEM;
+    h->g.lx = dims[0]; h->g.ly = dims[1]; h->g.lz = dims[2]; h->g.lt = dims[3];
+    h->g.V = (int)V;
+    h->g.bc_t = bc_t;
+    h->kappa = kappa;
+    h->prec = precision;
+    h->storage = precision == MPMC_FP64 ? ST_F64 : (precision == MPMC_FP32 ? ST_F32 : ST_BF16);
+    int rc = MPMC_OK;
+    auto bail = [&](int code) { mpmc_destroy(h); return code; };
+    if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(MPMC_ECUDA);
+    }
+    h->stream = h->own;
+    const size_t nl = (size_t)V * 36;   // complex link entries
+    double* staging = nullptr;
+    if ((rc = dev_alloc(h, &staging, nl * 16))) return bail(rc);
+    if (cudaMemcpy(staging, links, nl * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+        dev_free(staging);
+        return bail(MPMC_ECUDA);
+    }
+    if ((rc = dev_alloc(h, &h->links64, nl * 16))) { dev_free(staging); return bail(rc); }
+    launch_links(ST_F64, h->g.V, staging, h->links64, h->stream);
+    if (h->storage != ST_F64) {
+        if ((rc = dev_alloc(h, &h->links32, nl * 8))) { dev_free(staging); return bail(rc); }
+        launch_links(ST_F32, h->g.V, staging, h->links32, h->stream);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        dev_free(staging);
+        return bail(MPMC_ECUDA);
+    }
+    dev_free(staging);
+    *out = h;
+    return MPMC_OK;
+}
+
+int mpmc_destroy(mpmc_handle h) {
+    if (!h) return MPMC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_ws(h->ws);
+    free_ws(h->ws64);
+    free_deflation(h);
+    dev_free(h->links64);
+    dev_free(h->links32);
+    dev_free(h->samples);
+    dev_free(h->io);
+    dev_free(h->kr_part);
+    dev_free(h->kr_h);
+    dev_free(h->kr_nrm);
+    if (h->own) cudaStreamDestroy(h->own);
+    delete h;
+    return MPMC_OK;
+}
+
+int mpmc_set_stream(mpmc_handle h, void* stream) {
+    if (!h) return MPMC_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    h->stream = stream ? (cudaStream_t)stream : h->own;
+    return MPMC_OK;
+}
+
+int mpmc_set_block(mpmc_handle h, int nb) {
+    if (!h) return MPMC_EINVAL;
+    if (nb < 0 || nb > MPMC_MAX_BLOCK) return fail(h, MPMC_EINVAL, "block size out of range");
+    h->nb_user = nb;
+    return MPMC_OK;
+}
+
+int mpmc_set_poly(mpmc_handle h, int index, int kind, const double* roots, int nroots, const double* outer,
+                  int nouter, int leja) {
+    if (!h) return MPMC_EINVAL;
+    if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
+    if (kind != MPMC_SINGLE && kind != MPMC_COMPOSITE && kind != MPMC_DEFLATED_COMPOSITE)
+        return fail(h, MPMC_EINVAL, "unknown polynomial kind");
+    if (!roots || nroots < 1 || nroots > 100000) return fail(h, MPMC_EINVAL, "need at least one root");
+    if (kind != MPMC_SINGLE && (!outer || nouter < 1 || nouter > 100000))
+        return fail(h, MPMC_EINVAL, "composite polynomial needs outer roots");
+    if (kind == MPMC_DEFLATED_COMPOSITE && h->k == 0)
+        return fail(h, MPMC_ESTATE, "projected composite needs mpmc_set_deflation first");
+    if (kind == MPMC_DEFLATED_COMPOSITE && nouter < 2)
+        return fail(h, MPMC_EINVAL, "projected composite needs at least two outer roots");
+    PolyDef p;
+    p.kind = kind;
+    for (int i = 0; i < nroots; ++i) p.roots.emplace_back(roots[2 * i], roots[2 * i + 1]);
+    if (kind != MPMC_SINGLE)
+        for (int i = 0; i < nouter; ++i) p.outer.emplace_back(outer[2 * i], outer[2 * i + 1]);
+    for (const cd& z : p.roots)
+        if (!finite(z) || z == 0.0) return fail(h, MPMC_ENONFINITE, "root is zero or not finite");
+    for (const cd& z : p.outer)
+        if (!finite(z) || z == 0.0) return fail(h, MPMC_ENONFINITE, "outer root is zero or not finite");
+    if (leja) {
+        auto o = leja_order(p.roots);
+        std::vector<cd> r(p.roots.size());
+        for (size_t i = 0; i < o.size(); ++i) r[i] = p.roots[o[i]];
+        p.roots.swap(r);
+        if (!p.outer.empty()) {
+            auto oo = leja_order(p.outer);
+            std::vector<cd> q(p.outer.size());
+            for (size_t i = 0; i < oo.size(); ++i) q[i] = p.outer[oo[i]];
+            p.outer.swap(q);
+        }
+    }
+    p.set = true;
+    h->polys[index] = p;
+    return upload_coefficients(h);
+}
+
+int mpmc_get_roots(mpmc_handle h, int index, double* roots, double* outer) {
+    if (!h) return MPMC_EINVAL;
+    if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
+    const PolyDef& p = h->polys[index];
+    if (!p.set) return fail(h, MPMC_ESTATE, "polynomial not set");
+    if (roots)
+        for (size_t i = 0; i < p.roots.size(); ++i) { roots[2 * i] = p.roots[i].real(); roots[2 * i + 1] = p.roots[i].imag(); }
+    if (outer)
+        for (size_t i = 0; i < p.outer.size(); ++i) { outer[2 * i] = p.outer[i].real(); outer[2 * i + 1] = p.outer[i].imag(); }
+    return MPMC_OK;
+}
+
+int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+    if (!h) return MPMC_EINVAL;
+    const long long n = nsites12(h);
+    if (k < 0 || k > n || k > 4096) return fail(h, MPMC_EINVAL, "k out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    free_deflation(h);
+    for (int p = 0; p < MPMC_MAX_POLYS; ++p)
+        if (h->polys[p].set && h->polys[p].kind == MPMC_DEFLATED_COMPOSITE && k == 0)
+            return fail(h, MPMC_ESTATE, "a projected composite polynomial needs deflation vectors");
+    if (k == 0) return MPMC_OK;
+    if (!Z || !lambda || !pair) return fail(h, MPMC_EINVAL, "null deflation input");
+    for (int i = 0; i < k; ++i) {
+        if (pair[i] < 0 || pair[i] >= k) return fail(h, MPMC_EINVAL, "pair index out of range");
+        if (pair[pair[i]] != i) return fail(h, MPMC_EINVAL, "pair map is not an involution");
+        if (!std::isfinite(lambda[2 * i]) || !std::isfinite(lambda[2 * i + 1]) ||
+            (lambda[2 * i] == 0 && lambda[2 * i + 1] == 0))
+            return fail(h, MPMC_ENONFINITE, "eigenvalue is zero or not finite");
+    }
+    h->k = k;
+    for (int i = 0; i < k; ++i) h->lam.emplace_back(lambda[2 * i], lambda[2 * i + 1]);
+    h->pair.assign(pair, pair + k);
+    const size_t ncplx = (size_t)n * k;
+    const int zst = h->storage == ST_F64 ? ST_F64 : ST_F32;
+    if (int rc = ensure_io(h, ncplx)) return rc;
+    CK(cudaMemcpyAsync(h->io, Z, ncplx * 16, cudaMemcpyHostToDevice, h->stream));
+    if (int rc = dev_alloc(h, &h->Z, ncplx * (zst == ST_F64 ? 16 : 8))) return rc;
+    launch_convert_vectors(zst, ncplx, h->io, h->Z, h->stream);
+    LAUNCHED(1);
+    if (int rc = dev_alloc(h, &h->d_pair, sizeof(int) * k)) return rc;
+    CK(cudaMemcpyAsync(h->d_pair, pair, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
+    if (int rc = dev_alloc(h, &h->d_dnorm, sizeof(double2) * k)) return rc;
+    launch_defl_norms(zst, h->g.V, k, h->Z, h->d_pair, h->d_dnorm, h->stream);
+    LAUNCHED(1);
+    std::vector<double2> dn(k);
+    CK(cudaMemcpyAsync(dn.data(), h->d_dnorm, sizeof(double2) * k, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < k; ++i) {
+        h->dnorm.emplace_back(dn[i].x, dn[i].y);
+        if (!finite(h->dnorm[i]) || h->dnorm[i] == 0.0)
+            return fail(h, MPMC_ENONFINITE, "u_i^H z_i is zero or not finite");
+    }
+    if (int rc = dev_alloc(h, &h->d_coef, sizeof(double2) * (size_t)MPMC_MAX_POLYS * k)) return rc;
+    return upload_coefficients(h);
+}
+
+int mpmc_level_info(mpmc_handle h, int level, double* correction, long long* matvecs) {
+    if (!h) return MPMC_EINVAL;
+    const int L = num_levels(h);
+    if (L == 0) return fail(h, MPMC_ESTATE, "no polynomial set");
+    if (level < 0 || level >= L) return fail(h, MPMC_EINVAL, "level out of range");
+    if (correction) {
+        std::vector<cd> c;
+        if (int rc = level_coefficients(h, level, c)) return rc;
+        cd s = 0.0;
+        for (const cd& q : c) s += q;   // u_i^H z_i = 1 by the library's scaling
+        correction[0] = s.real();
+        correction[1] = s.imag();
+    }
+    if (matvecs) {
+        long long mv = spec_matvecs(h->polys[level]);
+        if (level + 1 < L) mv += spec_matvecs(h->polys[level + 1]);
+        *matvecs = mv;
+    }
+    return MPMC_OK;
+}
+
+int mpmc_apply_op(mpmc_handle h, const double* X, double* Y, int nrhs, int on_device) {
+    if (!h || !X || !Y || nrhs < 1) return h ? fail(h, MPMC_EINVAL, "bad apply_op arguments") : MPMC_EINVAL;
+    const size_t n = nsites12(h);
+    const int nb = std::min(default_nb(h), nrhs);
+    if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    const double* src = X;
+    double* dst = Y;
+    if (!on_device) {
+        if (int rc = ensure_io(h, n * nrhs)) return rc;
+        CK(cudaMemcpyAsync(h->io, X, n * nrhs * 16, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+        dst = h->io;
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += nb) {
+        const int cnt = std::min(nb, nrhs - c0);
+        launch_import(h->storage, h->g.V, src, nrhs, c0, cnt, h->ws.w[2], nb, h->stream);
+        LAUNCHED(1);
+        if (int rc = apply_A(h, h->ws, h->ws.w[2], h->ws.w[3])) return rc;
+        launch_export(h->storage, h->g.V, h->ws.w[3], nb, dst, nrhs, c0, cnt, h->stream);
+        LAUNCHED(1);
+    }
+    if (!on_device) CK(cudaMemcpyAsync(Y, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPMC_OK;
+}
+
+int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nrhs, int on_device) {
+    if (!h) return MPMC_EINVAL;
+    if (!B || !X || nrhs < 1) return fail(h, MPMC_EINVAL, "bad apply_poly arguments");
+    if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
+    const PolyDef& p = h->polys[index];
+    if (!p.set) return fail(h, MPMC_ESTATE, "polynomial not set");
+    if (p.kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "projected composite apply not built yet");
+    const size_t n = nsites12(h);
+    const int nb = std::min(default_nb(h), nrhs);
+    if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    const double* src = B;
+    double* dst = X;
+    if (!on_device) {
+        if (int rc = ensure_io(h, n * nrhs)) return rc;
+        CK(cudaMemcpyAsync(h->io, B, n * nrhs * 16, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+        dst = h->io;
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += nb) {
+        const int cnt = std::min(nb, nrhs - c0);
+        launch_import(h->storage, h->g.V, src, nrhs, c0, cnt, h->ws.r, nb, h->stream);
+        LAUNCHED(1);
+        if (int rc = chain_apply(h, h->ws, p, h->ws.r, h->ws.x)) return rc;
+        launch_export(h->storage, h->g.V, h->ws.x, nb, dst, nrhs, c0, cnt, h->stream);
+        LAUNCHED(1);
+    }
+    if (!on_device) CK(cudaMemcpyAsync(X, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPMC_OK;
+}
+
+int mpmc_noise(mpmc_handle h, uint64_t seed, int level, int first, int nrhs, double* B, int on_device) {
+    if (!h) return MPMC_EINVAL;
+    if (!B || nrhs < 1 || level < 0 || first < 0) return fail(h, MPMC_EINVAL, "bad noise arguments");
+    const size_t n = nsites12(h);
+    double* dst = B;
+    if (!on_device) {
+        if (int rc = ensure_io(h, n * nrhs)) return rc;
+        dst = h->io;
+    }
+    NoiseSpec ns{seed, (uint32_t)level, (uint32_t)first};
+    launch_noise_f64(h->g, ns, nrhs, nrhs, 0, dst, h->stream);
+    LAUNCHED(1);
+    if (!on_device) CK(cudaMemcpyAsync(B, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPMC_OK;
+}
+
+int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, double* mean, double* var,
+                      double* samples) {
+    if (!h) return MPMC_EINVAL;
+    if (nsamples < 1 || first < 0) return fail(h, MPMC_EINVAL, "nsamples must be >= 1 and first >= 0");
+    const int L = num_levels(h);
+    if (L == 0) return fail(h, MPMC_ESTATE, "no polynomial set");
+    for (int l = 0; l < L; ++l)
+        if (h->polys[l].kind == MPMC_DEFLATED_COMPOSITE)
+            return fail(h, MPMC_ENOTSUP, "projected composite trace not built yet");
+    const int nb = std::min(default_nb(h), nsamples);
+    if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    if (int rc = ensure_defl_work(h, nb)) return rc;
+    const size_t need = (size_t)L * nsamples;
+    if (h->samples_cap < need) {
+        dev_free(h->samples);
+        h->samples_cap = 0;
+        if (int rc = dev_alloc(h, &h->samples, sizeof(double2) * need)) return rc;
+        h->samples_cap = need;
+    }
+    Workspace& ws = h->ws;
+    const int nsplit = defl_nsplit(h->g.V);
+    for (int l = 0; l < L; ++l) {
+        const bool has_lo = l + 1 < L;
+        const bool defl = has_lo && h->k > 0;
+        for (int b0 = 0; b0 < nsamples; b0 += nb) {
+            const int nvalid = std::min(nb, nsamples - b0);
+            const NoiseSpec ns{seed, (uint32_t)l, (uint32_t)(first + b0)};
+            cd c_hi = 0.0, c_lo = 0.0;
+            if (int rc = chain_trace(h, ws, h->polys[l], ns, nullptr, ws.acc_hi, &c_hi)) return rc;
+            if (has_lo)
+                if (int rc = chain_trace(h, ws, h->polys[l + 1], ns, nullptr, ws.acc_lo, &c_lo)) return rc;
+            if (defl) {
+                launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part,
+                                 nsplit, h->stream);
+                launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1,
+                                   h->G2, h->dterm, h->stream);
+                LAUNCHED(3);
+            }
+            double chi[2], clo[2];
+            setc(chi, c_hi);
+            setc(clo, c_lo);
+            launch_finalize(ws.acc_rows, nb, nvalid, ws.acc_hi, has_lo ? ws.acc_lo : nullptr, chi, clo,
+                            defl ? h->dterm : nullptr, h->samples + (size_t)l * nsamples + b0, nullptr, nullptr,
+                            h->stream);
+            LAUNCHED(1);
+        }
+    }
+    std::vector<double2> hs(need);
+    CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < need; ++i)
+        if (!std::isfinite(hs[i].x) || !std::isfinite(hs[i].y)) return fail(h, MPMC_ENONFINITE, "non-finite sample");
+    for (int l = 0; l < L; ++l) {
+        const double2* s = hs.data() + (size_t)l * nsamples;
+        double mr = 0, mi = 0;
+        for (int j = 0; j < nsamples; ++j) { mr += s[j].x; mi += s[j].y; }
+        mr /= nsamples;
+        mi /= nsamples;
+        double v = NAN;
+        if (nsamples > 1) {
+            v = 0;
+            for (int j = 0; j < nsamples; ++j) v += (s[j].x - mr) * (s[j].x - mr);
+            v /= (nsamples - 1);
+        }
+        double corr[2] = {0, 0};
+        if (int rc = mpmc_level_info(h, l, corr, nullptr)) return rc;
+        if (mean) { mean[2 * l] = mr + corr[0]; mean[2 * l + 1] = mi + corr[1]; }
+        if (var) var[l] = v;
+        if (samples)
+            for (int j = 0; j < nsamples; ++j) {
+                samples[2 * ((size_t)l * nsamples + j)] = s[j].x;
+                samples[2 * ((size_t)l * nsamples + j) + 1] = s[j].y;
+            }
+    }
+    return MPMC_OK;
+}
+
+int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m, double* hbar, double* basis, int* steps) {
+    if (!h) return MPMC_EINVAL;
+    if (!v0 || !hbar || m < 1 || m > 4096) return fail(h, MPMC_EINVAL, "bad arnoldi arguments");
+    if (op_poly >= MPMC_MAX_POLYS || (op_poly >= 0 && !h->polys[op_poly].set))
+        return fail(h, MPMC_ESTATE, "operator polynomial not set");
+    if (op_poly >= 0 && h->polys[op_poly].kind == MPMC_DEFLATED_COMPOSITE)
+        return fail(h, MPMC_ENOTSUP, "arnoldi on a projected composite is not supported");
+    const size_t n = nsites12(h);
+    if (int rc = ensure_ws(h, h->ws64, ST_F64, 1)) return rc;
+    double2* Vb = reinterpret_cast<double2*>(basis);
+    double2* own = nullptr;
+    if (!Vb) {
+        if (int rc = dev_alloc(h, &own, sizeof(double2) * n * (m + 1))) return rc;
+        Vb = own;
+    }
+    if (h->kr_m < m + 1) {
+        dev_free(h->kr_part);
+        dev_free(h->kr_h);
+        dev_free(h->kr_nrm);
+        h->kr_m = 0;
+        const int np = mdot_parts(n);
+        if (int rc = dev_alloc(h, &h->kr_part, sizeof(double2) * (size_t)np * (m + 1))) { dev_free(own); return rc; }
+        if (int rc = dev_alloc(h, &h->kr_h, sizeof(double2) * 2 * (m + 1))) { dev_free(own); return rc; }
+        if (int rc = dev_alloc(h, &h->kr_nrm, sizeof(double) * (np + 1))) { dev_free(own); return rc; }
+        h->kr_m = m + 1;
+    }
+    int rc = MPMC_OK;
+    std::fill(hbar, hbar + 2 * (size_t)(m + 1) * m, 0.0);
+    Workspace& ws = h->ws64;
+    double2* w = reinterpret_cast<double2*>(ws.w[2]);
+    double2* tmp = reinterpret_cast<double2*>(ws.w[3]);
+    double* part = reinterpret_cast<double*>(h->kr_part);
+    double* nrm = h->kr_nrm;
+    std::vector<double2> h1(m + 1), h2(m + 1);
+    int done = 0;
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(w, v0, n * 16, cudaMemcpyHostToDevice, h->stream));
+        launch_norm2(n, w, part, nrm, h->stream);
+        launch_normalize(n, w, nrm, Vb, h->stream);
+        LAUNCHED(3);
+        for (int j = 0; j < m; ++j) {
+            double2* vj = Vb + (size_t)j * n;
+            if (op_poly < 0) {
+                if (int e = apply_A(h, ws, vj, w)) return e;
+            } else {
+                if (int e = chain_apply(h, ws, h->polys[op_poly], vj, ws.r)) return e;
+                if (int e = apply_A(h, ws, ws.r, w)) return e;
+            }
+            // two passes of classical Gram-Schmidt
+            launch_mdot(n, j + 1, Vb, w, h->kr_part, h->kr_h, h->stream);
+            launch_maxpy(n, j + 1, Vb, h->kr_h, w, h->stream);
+            CK(cudaMemcpyAsync(h1.data(), h->kr_h, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, h->stream));
+            launch_mdot(n, j + 1, Vb, w, h->kr_part, h->kr_h + (m + 1), h->stream);
+            launch_maxpy(n, j + 1, Vb, h->kr_h + (m + 1), w, h->stream);
+            CK(cudaMemcpyAsync(h2.data(), h->kr_h + (m + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost,
+                               h->stream));
+            launch_norm2(n, w, part, nrm, h->stream);
+            LAUNCHED(8);
+            double nn = 0;
+            CK(cudaMemcpyAsync(&nn, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (int i = 0; i <= j; ++i) {
+                hbar[2 * ((size_t)i * m + j)] = h1[i].x + h2[i].x;
+                hbar[2 * ((size_t)i * m + j) + 1] = h1[i].y + h2[i].y;
+            }
+            const double beta = std::sqrt(nn);
+            hbar[2 * ((size_t)(j + 1) * m + j)] = beta;
+            done = j + 1;
+            if (!(beta > 0) || !std::isfinite(beta)) break;
+            launch_normalize(n, w, nrm, Vb + (size_t)(j + 1) * n, h->stream);
+            LAUNCHED(1);
+            (void)tmp;
+        }
+        CK(cudaStreamSynchronize(h->stream));
+        return MPMC_OK;
+    };
+    rc = body();
+    dev_free(own);
+    if (steps) *steps = done;
+    return rc;
+}
+
+int mpmc_combine(mpmc_handle h, const double* Vb, int m, const double* Y, int k, double* Z) {
+    if (!h) return MPMC_EINVAL;
+    if (!Vb || !Y || !Z || m < 1 || k < 1) return fail(h, MPMC_EINVAL, "bad combine arguments");
+    const size_t n = nsites12(h);
+    double2* dY = nullptr;
+    if (int rc = dev_alloc(h, &dY, sizeof(double2) * (size_t)m * k)) return rc;
+    int rc = cuda_check(h, cudaMemcpyAsync(dY, Y, sizeof(double2) * (size_t)m * k, cudaMemcpyHostToDevice, h->stream),
+                        "copy Y");
+    if (!rc) {
+        launch_combine(n, m, reinterpret_cast<const double2*>(Vb), dY, k, reinterpret_cast<double2*>(Z), h->stream);
+        h->launches += 1;
+        rc = cuda_check(h, cudaGetLastError(), "combine");
+        if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "combine");
+    }
+    dev_free(dY);
+    return rc;
+}
+
+}  // extern "C"

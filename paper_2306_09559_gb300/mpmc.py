@@ -1,0 +1,237 @@
+"""Thin ctypes binding of libmpmc.so (the C ABI of include/mpmc.h).
+
+Only argument marshalling happens here: numpy arrays become host pointers,
+torch CUDA tensors become device pointers, and every computation runs in
+the library's CUDA kernels.  If the library is missing, :func:`lib` raises;
+there is no fallback path.
+
+Vector blocks use the library layout: complex128 arrays of shape
+(V, 4, 3, nrhs) (site, spin, colour, column), i.e. an n x nrhs matrix in
+unknown order with the column index fastest.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPMC_OK, MPMC_EINVAL, MPMC_ENOMEM, MPMC_ENOTSUP, MPMC_ETIMEOUT, MPMC_ENONFINITE, MPMC_ECUDA, MPMC_ESTATE = range(8)
+FP64, FP32, BF16S = 0, 1, 2
+SINGLE, COMPOSITE, DEFLATED_COMPOSITE = 0, 1, 2
+MAX_POLYS = 8
+MAX_BLOCK = 1024
+
+_LIB = None
+
+_SIGS = {
+    "mpmc_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "mpmc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "mpmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mpmc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "mpmc_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_set_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mpmc_set_poly": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "mpmc_get_roots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_set_deflation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int]),
+    "mpmc_apply_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "mpmc_apply_poly": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int]),
+    "mpmc_trace_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_level_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_longlong)]),
+    "mpmc_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_int]),
+    "mpmc_arnoldi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "mpmc_combine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_void_p]),
+    "mpmc_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+}
+
+
+def exported_symbols():
+    """Names every build of the library must export (the declarations of include/mpmc.h)."""
+    return sorted(_SIGS)
+
+
+def lib(path=None):
+    """The loaded library (loaded once).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2306_09559_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+class MpmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _ptr(a):
+    """Host pointer of a C-contiguous numpy array, or device pointer of a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _is_device(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Handle:
+    """One lattice: links, kappa, precision (mpmc_create ... mpmc_destroy)."""
+
+    def __init__(self, links, kappa, precision=FP64, bc_t=1):
+        L = lib()
+        links = _c128(links)
+        lt, lz, ly, lx = links.shape[1:5]
+        self.dims = (lx, ly, lz, lt)
+        self.V = lx * ly * lz * lt
+        self.n = 12 * self.V
+        self.precision = precision
+        self.kappa = kappa
+        dims = (ctypes.c_int * 4)(lx, ly, lz, lt)
+        h = ctypes.c_void_p()
+        rc = L.mpmc_create(ctypes.byref(h), dims, _ptr(links), float(kappa), int(precision), int(bc_t))
+        if rc != MPMC_OK:
+            raise MpmcError(rc, "mpmc_create: " + L.mpmc_strerror(rc).decode())
+        self._h = h
+        self._L = L
+        self.nlevels = 0
+
+    def _check(self, rc, what):
+        if rc != MPMC_OK:
+            msg = self._L.mpmc_last_error(self._h).decode()
+            raise MpmcError(rc, f"{what}: {self._L.mpmc_strerror(rc).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mpmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ----------------------------------------------------------------- config
+    def mpmc_set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.mpmc_set_stream(self._h, ctypes.c_void_p(raw) if raw else None), "mpmc_set_stream")
+
+    def mpmc_set_block(self, nb):
+        self._check(self._L.mpmc_set_block(self._h, int(nb)), "mpmc_set_block")
+
+    def mpmc_set_poly(self, index, kind, roots, outer=None, leja=True):
+        r = _c128(roots)
+        o = _c128(outer) if outer is not None else None
+        rc = self._L.mpmc_set_poly(self._h, int(index), int(kind), _ptr(r), r.size, _ptr(o),
+                                   0 if o is None else o.size, 1 if leja else 0)
+        self._check(rc, "mpmc_set_poly")
+        self.nlevels = max(self.nlevels, index + 1)
+
+    def mpmc_get_roots(self, index, nroots, nouter=0):
+        r = np.zeros(nroots, dtype=np.complex128)
+        o = np.zeros(max(nouter, 1), dtype=np.complex128)
+        self._check(self._L.mpmc_get_roots(self._h, int(index), _ptr(r), _ptr(o)), "mpmc_get_roots")
+        return (r, o[:nouter]) if nouter else r
+
+    def mpmc_set_deflation(self, Z, lam, pair):
+        """Z: n x k complex (column i = z_i), lam: k, pair: k ints."""
+        Z = np.asarray(Z)
+        k = 0 if Z.size == 0 else Z.shape[1]
+        Zt = _c128(Z.T) if k else None
+        lam = _c128(lam) if k else None
+        pr = np.ascontiguousarray(pair, dtype=np.int32) if k else None
+        self._check(self._L.mpmc_set_deflation(self._h, _ptr(Zt), _ptr(lam), _ptr(pr), k), "mpmc_set_deflation")
+
+    # ----------------------------------------------------------------- compute
+    def _block_call(self, fn, what, X, *pre):
+        if _is_device(X):
+            import torch
+            nrhs = X.shape[-1] if X.dim() > 1 else 1
+            Y = torch.empty_like(X)
+            self._check(fn(self._h, *pre, _ptr(X), _ptr(Y), nrhs, 1), what)
+            return Y
+        X = _c128(X)
+        nrhs = X.shape[-1] if X.ndim > 1 else 1
+        Y = np.empty_like(X)
+        self._check(fn(self._h, *pre, _ptr(X), _ptr(Y), nrhs, 0), what)
+        return Y
+
+    def mpmc_apply_op(self, X):
+        """A X for X of shape (n, nrhs) (or (n,)), host numpy or device torch complex128."""
+        return self._block_call(self._L.mpmc_apply_op, "mpmc_apply_op", X)
+
+    def mpmc_apply_poly(self, index, B):
+        return self._block_call(self._L.mpmc_apply_poly, "mpmc_apply_poly", B, int(index))
+
+    def mpmc_trace_levels(self, seed, nsamples, first=0, want_samples=True):
+        L = self.nlevels
+        mean = np.zeros(L, dtype=np.complex128)
+        var = np.zeros(L, dtype=np.float64)
+        samples = np.zeros((L, nsamples), dtype=np.complex128) if want_samples else None
+        rc = self._L.mpmc_trace_levels(self._h, ctypes.c_uint64(seed), int(nsamples), int(first), _ptr(mean),
+                                       _ptr(var), _ptr(samples))
+        self._check(rc, "mpmc_trace_levels")
+        return mean, var, samples
+
+    def mpmc_level_info(self, level):
+        corr = np.zeros(1, dtype=np.complex128)
+        mv = ctypes.c_longlong()
+        self._check(self._L.mpmc_level_info(self._h, int(level), _ptr(corr), ctypes.byref(mv)), "mpmc_level_info")
+        return corr[0], mv.value
+
+    def mpmc_noise(self, seed, level, first, nrhs):
+        B = np.zeros((self.n, nrhs), dtype=np.complex128)
+        self._check(self._L.mpmc_noise(self._h, ctypes.c_uint64(seed), int(level), int(first), int(nrhs), _ptr(B), 0),
+                    "mpmc_noise")
+        return B
+
+    def mpmc_arnoldi(self, op_poly, v0, m, basis=None):
+        """Hbar ((m+1) x m) and completed steps; basis: optional torch complex128 (m+1, n) device tensor."""
+        v0 = _c128(v0)
+        hbar = np.zeros((m + 1, m), dtype=np.complex128)
+        steps = ctypes.c_int()
+        rc = self._L.mpmc_arnoldi(self._h, int(op_poly), _ptr(v0), int(m), _ptr(hbar), _ptr(basis),
+                                  ctypes.byref(steps))
+        self._check(rc, "mpmc_arnoldi")
+        return hbar, steps.value
+
+    def mpmc_combine(self, basis, m, Y, Z):
+        """Z (device, (k, n)) = sum_j basis[j] Y[j, :] for j < m."""
+        Y = _c128(Y)
+        self._check(self._L.mpmc_combine(self._h, _ptr(basis), int(m), _ptr(Y), Y.shape[1], _ptr(Z)), "mpmc_combine")
+
+    def mpmc_launch_count(self):
+        return int(self._L.mpmc_launch_count(self._h))
