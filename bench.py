@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Benchmark of the Multipolynomial Monte Carlo hot path on GB300.
+
+One step = one pass over every level of the multilevel trace estimate
+(Eq. (2)) for one batch of Z4 noise vectors: the composite and single
+polynomial chains fused into the Wilson stencil, the deflation dots, the
+per-sample assembly and the per-level statistics, all through the C ABI
+(mpmc_trace_levels).  Default workload: the 8^4 lattice with levels
+composite 20x10 (degree 199), degree 50 and degree 10, 50 deflation
+eigenpairs and 512 noise vectors per level.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead (bounded sample of the same workload).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "noise-vector poly applies/s, dslash HBM GB/s; mixed vs FP64 at equal trace err"
+UNIT = "noise-vector poly applies/s"
+FLOPS_PER_SITE_RHS_STEP = 1488   # 1320 hopping + 48 diagonal + 96 chain axpy + 24 Z4 dot
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = self.proc.communicate()[0]
+
+    def summary(self):
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ------------------------------------------------------------------ oracle leg
+def oracle_worker(spec):
+    """Runs in a fresh single-threaded process: the oracle, as it stands, on a bounded sample."""
+    import numpy as np
+    from oracle import krylov as K
+    from oracle import mpmc as M
+    from oracle.lattice import WilsonOperator
+    from paper_2306_09559_gb300 import workloads, synth
+
+    wl = workloads.get(spec["workload"])
+    per_level = spec["per_level"]
+    U = workloads.gauge(wl)
+    op = WilsonOperator(U, wl.kappa)
+    t0 = time.perf_counter()
+    b0 = synth.random_unit_vector(op.n, wl.setup_seed)
+    singles = [lv[1] for lv in wl.levels if lv[0] == "single"]
+    inners = [lv[1] - 1 for lv in wl.levels if lv[0] == "composite"]
+    degs = sorted(set(singles + inners))
+    V, Hbar, beta = K.arnoldi(op, b0, max(degs) + 1)
+    roots = {d: K.harmonic_ritz(Hbar, d + 1) for d in degs}
+    polys = []
+    for lv in wl.levels:
+        if lv[0] == "single":
+            polys.append({"kind": "single", "roots": roots[lv[1]][P_leja(roots[lv[1]])]})
+        else:
+            inner = roots[lv[1] - 1][P_leja(roots[lv[1] - 1])]
+            outer, _, _ = K.pp_gmres_roots(op, inner, b0, m_out=lv[2])
+            polys.append({"kind": "composite", "inner": inner, "outer": outer})
+    defl = None
+    if wl.k > 0:
+        # deflation vectors of the workload's shape (k orthonormal Krylov vectors); the
+        # cost of a sample depends on k and n, not on how accurate the vectors are
+        Zk = V[:, :wl.k]
+        lam = np.einsum("ni,ni->i", Zk.conj(), op(Zk))
+        defl = M.Deflation(op, Zk, lam, np.arange(wl.k))
+    t_setup = time.perf_counter() - t0
+    times = []
+    for step in range(spec["steps"]):
+        t1 = time.perf_counter()
+        for level in range(len(polys)):
+            M.level_sample_parts(op, polys, level, wl.noise_seed, per_level, defl, first=step * per_level,
+                                 block=per_level)
+        times.append(time.perf_counter() - t1)
+    applies = per_level * (2 * (len(polys) - 1) + 1)
+    return {"times": times, "applies_per_step": applies, "setup_s": t_setup}
+
+
+def P_leja(r):
+    from oracle import polynomial as P
+    return P.leja_order(r)
+
+
+def run_oracle(workload, per_level, steps):
+    """The oracle leg in a subprocess with one BLAS/OpenMP thread (cores = 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    with tempfile.NamedTemporaryFile("r", suffix=".json", delete=False) as f:
+        path = f.name
+    spec = json.dumps({"workload": workload, "per_level": per_level, "steps": steps, "out": path})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec], env=env,
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + r.stderr[-4000:])
+    out = json.load(open(path))
+    os.unlink(path)
+    return out
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2306_09559_gb300 import workloads
+    wl = workloads.get(args.workload)
+    per_level = args.oracle_noises
+    res = run_oracle(args.workload, per_level, args.steps + args.warmup)
+    times = res["times"][args.warmup:]
+    value = res["applies_per_step"] * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.describe(), "sample": f"{per_level} noise vectors per level per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_level} noises/level of the workload per step (FP64 numpy oracle, "
+                                   f"1 thread, {cpu_model()})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # the oracle process for the CPU baseline is started before any GPU work
+    oracle_proc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        tmp = tempfile.NamedTemporaryFile("r", suffix=".json", delete=False)
+        tmp.close()
+        spec = json.dumps({"workload": args.workload, "per_level": args.oracle_noises, "steps": 1,
+                           "out": tmp.name})
+        oracle_proc = (subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                                        env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True),
+                       tmp.name)
+
+    from paper_2306_09559_gb300 import build, workloads
+    from paper_2306_09559_gb300 import mpmc as G
+    build.build()
+    wl = workloads.get(args.workload)
+    block = args.block or wl.block
+    U = workloads.gauge(wl)
+    t0 = time.perf_counter()
+    h64 = G.Handle(U, wl.kappa, G.FP64)
+    polys, defl = workloads.setup(h64, wl, log=log if rank == 0 else None)
+    t_setup = time.perf_counter() - t0
+    prec = {"fp32": G.FP32, "bf16s": G.BF16S, "fp64": G.FP64}[args.precision]
+    hm = G.Handle(U, wl.kappa, prec)
+    stream = torch.cuda.Stream()
+    hm.mpmc_set_stream(stream)
+    workloads.configure(hm, polys, defl, block)
+    first = rank * wl.nsamples           # weak scaling: each rank draws its own noise indices
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def one(h, fst):
+        return h.mpmc_trace_levels(wl.noise_seed, wl.nsamples, fst)
+
+    for _ in range(args.warmup):
+        one(hm, first)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = hm.mpmc_launch_count()
+    hm.mpmc_profile(True)
+    results = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[k][0].record(stream)
+            results.append(one(hm, first))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = hm.mpmc_launch_count() - l0
+    st_ms, st_n, st_bytes = hm.mpmc_profile_read(G.PROF_STENCIL)
+    df_ms, df_n, df_bytes = hm.mpmc_profile_read(G.PROF_DEFLATION)
+    hm.mpmc_profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms)
+    t_max = t_local
+    if dist is not None:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * wl.applies_per_step() * args.steps / (t_max / 1000.0)
+
+    # ---------------------------------------------------------- end to end through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        Zp = None
+        if defl is not None:
+            Z, lam, pair = defl
+            Zp = torch.from_numpy(np.ascontiguousarray(Z.T)).pin_memory()
+            lamp, pairp = np.ascontiguousarray(lam), np.ascontiguousarray(pair, dtype=np.int32)
+        Up = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
+        h2d = Up.numel() * 16 + (Zp.numel() * 16 + lamp.size * 16 + pairp.size * 4 if Zp is not None else 0)
+        h2d += sum(16 * (r.size + (0 if o is None else o.size)) for _, r, o in polys)
+        d2h = 16 * wl.nsamples * len(polys)
+
+        def e2e_step():
+            hm.mpmc_set_links(Up)
+            if Zp is not None:
+                hm.mpmc_set_deflation(Zp, lamp, pairp, rows=True)
+            workloads.configure(hm, polys, None)
+            return one(hm, first)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - te
+        if dist is not None:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * wl.applies_per_step() * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000 * te / args.steps}
+
+    # ---------------------------------------------------------- FP64 path at equal trace error
+    fp64 = None
+    if not args.no_fp64 and prec != G.FP64:
+        workloads.configure(h64, polys, defl, block)
+        s64 = torch.cuda.Stream()
+        h64.mpmc_set_stream(s64)
+        one(h64, first)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s64)
+        m64, v64, x64 = one(h64, first)
+        b.record(s64)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b)
+        m32, v32, x32 = results[-1]
+        d = x32 - x64
+        var64, var32 = float(np.sum(v64)), float(np.sum(v32))
+        fp64 = {"value": wl.applies_per_step() / (t64 / 1000.0), "ms_per_step": t64,
+                "equal_se_speedup": (t64 * var64) / (ms_per_step * var32),
+                "level_var_fp64": [float(x) for x in v64], "level_var_mixed": [float(x) for x in v32],
+                "paired_mean_diff_over_se": [float(abs(np.mean(d[l].real)) / np.sqrt(v64[l] / wl.nsamples))
+                                             for l in range(len(polys))],
+                "paired_std_diff_over_std": [float(np.std(d[l].real) / np.sqrt(v64[l])) for l in range(len(polys))],
+                "level_estimates_fp64": [[float(z.real), float(z.imag)] for z in m64],
+                "level_estimates_mixed": [[float(z.real), float(z.imag)] for z in m32]}
+
+    # ---------------------------------------------------------- roofline of the dominant kernel
+    hbm, sm_max, src = peaks()
+    avg_ms = st_ms / max(st_n, 1)
+    bytes_per_launch = st_bytes / max(st_n, 1)
+    achieved_gbs = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "traffic": args.traffic, "kernel": "k_step/k_outer (fused stencil step)",
+                "peak_source": src, "avg_launch_ms": avg_ms, "launches": st_n,
+                "share_of_step": st_ms / t_local if t_local else None,
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    cpu = None
+    if oracle_proc is not None:
+        proc, path = oracle_proc
+        _, err = proc.communicate()
+        if proc.returncode == 0:
+            res = json.load(open(path))
+            tt = res["times"]
+            cpu = {"value": res["applies_per_step"] * len(tt) / sum(tt), "unit": UNIT, "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"{args.oracle_noises} noise vectors per level of the same workload, FP64 numpy oracle, "
+                             f"1 thread, {cpu_model()}"}
+        else:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
+        os.unlink(path)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16s": "bf16-stored/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": wl.describe(), "lattice": "x".join(map(str, wl.dims)),
+                       "noises_per_level": wl.nsamples, "levels": [list(x) for x in wl.levels],
+                       "deflation_k": wl.k, "nrhs_per_launch": block, "l2": "flushed before every step (256 MB write)",
+                       "parallelism": f"noise sharding x{world}", "matvecs_per_step": wl.matvecs_per_step(),
+                       "setup_s": t_setup},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "dslash_hbm_gbs": achieved_gbs, "cpu_baseline": cpu, "fp64": fp64,
+            "deflation_kernel": {"ms_per_step": df_ms / args.steps, "launches": df_n,
+                                 "achieved_gbs": (df_bytes / (df_ms / 1000.0) / 1e9) if df_ms else None},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpmc", choices=["mpmc", "reference"])
+    ap.add_argument("--workload", default="8^4")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16s", "fp64"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--oracle-noises", type=int, default=2)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture of this build")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_worker:
+        spec = json.loads(args.oracle_worker)
+        json.dump(oracle_worker(spec), open(spec["out"], "w"))
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.warmup < 3:
+        log("note: fewer than 3 warm-up steps")
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -235,6 +235,26 @@ MPMC_API int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m,
  */
 MPMC_API int mpmc_combine(mpmc_handle h, const double* Vb, int m, const double* Y, int k, double* Z);
 
+/*
+ * mpmc_set_links: replace the gauge links of h (same lattice; layout and
+ * copy semantics as in mpmc_create).  Polynomials and deflation vectors
+ * are kept: they belong to the caller's setup for the new field.
+ */
+MPMC_API int mpmc_set_links(mpmc_handle h, const double* links);
+
+/*
+ * Profiling: with mpmc_profile(h, 1) every kernel launch of the classes
+ * below is bracketed by CUDA events on the handle's stream; the elapsed
+ * device time, the launch count and the algorithmic bytes of the launches
+ * (vector reads and writes counted once per launch, links once per launch,
+ * deflation vectors once per launch) accumulate until mpmc_profile(h, 1)
+ * clears them; mpmc_profile(h, 0) stops recording.  mpmc_profile_read
+ * synchronises the stream and returns the totals of one class.
+ */
+enum { MPMC_PROF_STENCIL = 0, MPMC_PROF_DEFLATION = 1, MPMC_PROF_OTHER = 2 };
+MPMC_API int mpmc_profile(mpmc_handle h, int enable);
+MPMC_API int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* launches, double* bytes);
+
 /* Device counter of kernel launches made by the library since the handle
  * was created (the count a caller reports for its timed region). */
 MPMC_API long long mpmc_launch_count(mpmc_handle h);

@@ -83,6 +83,15 @@ struct mpmc_ctx {
     double* kr_nrm = nullptr;
     int kr_m = 0;
     long long launches = 0;
+    // profiling: events around kernel launches of each class (mpmc_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    std::vector<int> ev_cls;
+    std::vector<double> ev_bytes;
+    double prof_ms[3] = {0, 0, 0};
+    long long prof_n[3] = {0, 0, 0};
+    double prof_b[3] = {0, 0, 0};
     std::string err;
 };
 
@@ -168,6 +177,67 @@ int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
 }
 
 const void* links_for(const mpmc_ctx* h, int storage) { return storage == ST_F64 ? h->links64 : h->links32; }
+
+
+// ------------------------------------------------------------------ profiling
+int prof_begin(mpmc_ctx* h, int cls, double bytes) {
+    if (!h->prof) return MPMC_OK;
+    while (h->ev.size() < h->ev_used + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->ev.push_back(e);
+    }
+    CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
+    h->ev_cls.push_back(cls);
+    h->ev_bytes.push_back(bytes);
+    return MPMC_OK;
+}
+
+int prof_end(mpmc_ctx* h) {
+    if (!h->prof) return MPMC_OK;
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+    h->ev_used += 2;
+    return MPMC_OK;
+}
+
+// call after the stream has been synchronised
+int prof_collect(mpmc_ctx* h) {
+    for (size_t i = 0; i < h->ev_cls.size(); ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
+        h->prof_ms[h->ev_cls[i]] += ms;
+        h->prof_n[h->ev_cls[i]] += 1;
+        h->prof_b[h->ev_cls[i]] += h->ev_bytes[i];
+    }
+    h->ev_cls.clear();
+    h->ev_bytes.clear();
+    h->ev_used = 0;
+    return MPMC_OK;
+}
+
+enum { PROF_STENCIL = 0, PROF_DEFLATION = 1, PROF_OTHER = 2 };
+
+double link_bytes(const mpmc_ctx* h, int st) { return (double)h->g.V * 36 * (st == ST_F64 ? 16 : 8); }
+
+int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
+    const int reads = (a.in ? 1 : 0) + (a.ymode == 2 ? 1 : 0);
+    const int writes = 1 + (a.ymode ? 1 : 0);
+    const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * (reads + writes) + link_bytes(h, ws.storage);
+    if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
+    launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
+    if (int rc = prof_end(h)) return rc;
+    LAUNCHED(1);
+    return MPMC_OK;
+}
+
+int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
+    const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
+    if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
+    launch_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.cfg, h->stream);
+    if (int rc = prof_end(h)) return rc;
+    LAUNCHED(1);
+    return MPMC_OK;
+}
 
 // ------------------------------------------------------------------ roots
 std::vector<int> leja_order(const std::vector<cd>& r) {
@@ -259,8 +329,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             setc(a.c, h->kappa * al);
             setc(a.dot_w, 1.0 / th[j]);
             a.acc = acc;
-            launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
-            LAUNCHED(1);
+            if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
         return MPMC_OK;
@@ -308,8 +377,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             const cd al = 1.0 / th[j - 1];
             setc(a.a, 1.0 - al);
             setc(a.c, h->kappa * al);
-            launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
-            LAUNCHED(1);
+            if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
         OuterArgs o{};
@@ -325,8 +393,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         o.dot = (k == m_out - 1);
         setc(o.dot_w, 1.0 / th[0]);
         o.acc = acc;
-        launch_outer(st, h->g, U, nb, ns, o, cfg, h->stream);
-        LAUNCHED(1);
+        if (int rc = do_outer(h, ws, o, ns)) return rc;
         // never write into the caller's start buffer: alternate between w[2] and w[3]
         Wcur = Wnxt;
         Wnxt = (Wcur == ws.w[3]) ? ws.w[2] : ws.w[3];
@@ -344,8 +411,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         setc(a.c, h->kappa * al);
         setc(a.dot_w, 1.0 / th[j]);
         a.acc = acc;
-        launch_step(st, h->g, U, nb, ns, a, cfg, h->stream);
-        LAUNCHED(1);
+        if (int rc = do_step(h, ws, a, ns)) return rc;
         in = a.out;
     }
     return MPMC_OK;
@@ -378,8 +444,7 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
         setc(a.c, h->kappa * al);
         setc(a.ya, 1.0 / th[0]);
         setc(a.yb, 1.0 / th[j]);
-        launch_step(st, h->g, U, nb, ns, a, ws.cfg, h->stream);
-        LAUNCHED(1);
+        if (int rc = do_step(h, ws, a, ns)) return rc;
         in = a.out;
     }
     return MPMC_OK;
@@ -409,8 +474,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
             const cd al = 1.0 / th[j - 1];
             setc(a.a, 1.0 - al);
             setc(a.c, h->kappa * al);
-            launch_step(st, h->g, U, nb, ns, a, ws.cfg, h->stream);
-            LAUNCHED(1);
+            if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
         OuterArgs o{};
@@ -424,8 +488,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
         setc(o.beta, 1.0 / eta[k - 1]);
         setc(o.gamma, 1.0 / eta[k]);
         o.dot = false;
-        launch_outer(st, h->g, U, nb, ns, o, ws.cfg, h->stream);
-        LAUNCHED(1);
+        if (int rc = do_outer(h, ws, o, ns)) return rc;
         Wcur = Wnxt;
         Wnxt = (Wcur == ws.w[2]) ? ws.w[3] : ws.w[2];
     }
@@ -440,9 +503,7 @@ int apply_A(mpmc_ctx* h, Workspace& ws, const void* in, void* out) {
     setc(a.a, 1.0);
     setc(a.c, -h->kappa);
     const NoiseSpec ns{0, 0, 0};
-    launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
-    LAUNCHED(1);
-    return MPMC_OK;
+    return do_step(h, ws, a, ns);
 }
 
 int default_nb(const mpmc_ctx* h) {
@@ -615,6 +676,7 @@ int mpmc_destroy(mpmc_handle h) {
     dev_free(h->kr_part);
     dev_free(h->kr_h);
     dev_free(h->kr_nrm);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own) cudaStreamDestroy(h->own);
     delete h;
     return MPMC_OK;
@@ -774,7 +836,7 @@ int mpmc_apply_op(mpmc_handle h, const double* X, double* Y, int nrhs, int on_de
     }
     if (!on_device) CK(cudaMemcpyAsync(Y, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    return MPMC_OK;
+    return prof_collect(h);
 }
 
 int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nrhs, int on_device) {
@@ -805,7 +867,7 @@ int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nr
     }
     if (!on_device) CK(cudaMemcpyAsync(X, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    return MPMC_OK;
+    return prof_collect(h);
 }
 
 int mpmc_noise(mpmc_handle h, uint64_t seed, int level, int first, int nrhs, double* B, int on_device) {
@@ -857,8 +919,11 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
             if (has_lo)
                 if (int rc = chain_trace(h, ws, h->polys[l + 1], ns, nullptr, ws.acc_lo, &c_lo)) return rc;
             if (defl) {
+                if (int rc = prof_begin(h, PROF_DEFLATION, (double)h->k * nsites12(h) * (h->storage == ST_F64 ? 16 : 8)))
+                    return rc;
                 launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part,
                                  nsplit, h->stream);
+                if (int rc = prof_end(h)) return rc;
                 launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1,
                                    h->G2, h->dterm, h->stream);
                 LAUNCHED(3);
@@ -875,6 +940,7 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
     std::vector<double2> hs(need);
     CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (int rc = prof_collect(h)) return rc;
     for (size_t i = 0; i < need; ++i)
         if (!std::isfinite(hs[i].x) || !std::isfinite(hs[i].y)) return fail(h, MPMC_ENONFINITE, "non-finite sample");
     for (int l = 0; l < L; ++l) {
@@ -963,6 +1029,7 @@ int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m, double* hb
             double nn = 0;
             CK(cudaMemcpyAsync(&nn, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
+            if (int e = prof_collect(h)) return e;
             for (int i = 0; i <= j; ++i) {
                 hbar[2 * ((size_t)i * m + j)] = h1[i].x + h2[i].x;
                 hbar[2 * ((size_t)i * m + j) + 1] = h1[i].y + h2[i].y;
@@ -1000,6 +1067,44 @@ int mpmc_combine(mpmc_handle h, const double* Vb, int m, const double* Y, int k,
     }
     dev_free(dY);
     return rc;
+}
+
+int mpmc_profile(mpmc_handle h, int enable) {
+    if (!h) return MPMC_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    if (int rc = prof_collect(h)) return rc;
+    if (enable) {
+        for (int c = 0; c < 3; ++c) { h->prof_ms[c] = 0; h->prof_n[c] = 0; h->prof_b[c] = 0; }
+    }
+    h->prof = enable != 0;
+    return MPMC_OK;
+}
+
+int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* launches, double* bytes) {
+    if (!h) return MPMC_EINVAL;
+    if (cls < 0 || cls > 2) return fail(h, MPMC_EINVAL, "profile class out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    if (int rc = prof_collect(h)) return rc;
+    if (ms) *ms = h->prof_ms[cls];
+    if (launches) *launches = h->prof_n[cls];
+    if (bytes) *bytes = h->prof_b[cls];
+    return MPMC_OK;
+}
+
+int mpmc_set_links(mpmc_handle h, const double* links) {
+    if (!h) return MPMC_EINVAL;
+    if (!links) return fail(h, MPMC_EINVAL, "null links");
+    const size_t nl = (size_t)h->g.V * 36;
+    if (int rc = ensure_io(h, nl)) return rc;
+    CK(cudaMemcpyAsync(h->io, links, nl * 16, cudaMemcpyHostToDevice, h->stream));
+    launch_links(ST_F64, h->g.V, h->io, h->links64, h->stream);
+    LAUNCHED(1);
+    if (h->links32) {
+        launch_links(ST_F32, h->g.V, h->io, h->links32, h->stream);
+        LAUNCHED(1);
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return MPMC_OK;
 }
 
 }  // extern "C"

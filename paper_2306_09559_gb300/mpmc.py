@@ -52,7 +52,13 @@ _SIGS = {
     "mpmc_combine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                     ctypes.c_void_p]),
     "mpmc_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mpmc_set_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mpmc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
 }
+
+PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
 
 
 def exported_symbols():
@@ -119,7 +125,15 @@ class Handle:
             raise MpmcError(rc, "mpmc_create: " + L.mpmc_strerror(rc).decode())
         self._h = h
         self._L = L
-        self.nlevels = 0
+        self._set = set()
+
+    @property
+    def nlevels(self):
+        """Levels of mpmc_trace_levels: polynomials 0..L-1 set without a gap."""
+        L = 0
+        while L in self._set:
+            L += 1
+        return L
 
     def _check(self, rc, what):
         if rc != MPMC_OK:
@@ -158,7 +172,7 @@ class Handle:
         rc = self._L.mpmc_set_poly(self._h, int(index), int(kind), _ptr(r), r.size, _ptr(o),
                                    0 if o is None else o.size, 1 if leja else 0)
         self._check(rc, "mpmc_set_poly")
-        self.nlevels = max(self.nlevels, index + 1)
+        self._set.add(int(index))
 
     def mpmc_get_roots(self, index, nroots, nouter=0):
         r = np.zeros(nroots, dtype=np.complex128)
@@ -166,11 +180,19 @@ class Handle:
         self._check(self._L.mpmc_get_roots(self._h, int(index), _ptr(r), _ptr(o)), "mpmc_get_roots")
         return (r, o[:nouter]) if nouter else r
 
-    def mpmc_set_deflation(self, Z, lam, pair):
-        """Z: n x k complex (column i = z_i), lam: k, pair: k ints."""
-        Z = np.asarray(Z)
-        k = 0 if Z.size == 0 else Z.shape[1]
-        Zt = _c128(Z.T) if k else None
+    def mpmc_set_deflation(self, Z, lam, pair, rows=False):
+        """Z: n x k complex (column i = z_i), lam: k, pair: k ints.
+
+        rows=True: Z is already k x n (vector i contiguous, the library
+        layout), e.g. a pinned torch tensor; it is passed without a copy.
+        """
+        if rows:
+            k = Z.shape[0]
+            Zt = Z if hasattr(Z, "data_ptr") else _c128(Z)
+        else:
+            Z = np.asarray(Z)
+            k = 0 if Z.size == 0 else Z.shape[1]
+            Zt = _c128(Z.T) if k else None
         lam = _c128(lam) if k else None
         pr = np.ascontiguousarray(pair, dtype=np.int32) if k else None
         self._check(self._L.mpmc_set_deflation(self._h, _ptr(Zt), _ptr(lam), _ptr(pr), k), "mpmc_set_deflation")
@@ -235,3 +257,17 @@ class Handle:
 
     def mpmc_launch_count(self):
         return int(self._L.mpmc_launch_count(self._h))
+
+    def mpmc_set_links(self, links):
+        """links: (4, Lt, Lz, Ly, Lx, 3, 3) complex128 numpy array or a pinned torch tensor of the same bytes."""
+        ptr = _ptr(links) if hasattr(links, "data_ptr") else _ptr(_c128(links))
+        self._check(self._L.mpmc_set_links(self._h, ptr), "mpmc_set_links")
+
+    def mpmc_profile(self, enable):
+        self._check(self._L.mpmc_profile(self._h, 1 if enable else 0), "mpmc_profile")
+
+    def mpmc_profile_read(self, cls):
+        ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        self._check(self._L.mpmc_profile_read(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
+                    "mpmc_profile_read")
+        return ms.value, n.value, b.value

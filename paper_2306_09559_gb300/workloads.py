@@ -1,0 +1,139 @@
+"""Workloads (seeded synthetic lattices with their polynomial levels) and their setup.
+
+Each workload names its lattice, gauge-field generator, kappa, the levels
+(highest degree first, Eq. (2)), the number of deflation eigenpairs and the
+noise vectors per level.  A composite level (m_in, m_out) has m_in roots
+of p_in and m_out roots of p_out, degree m_in * m_out - 1 (Sec. 3.2).
+
+``setup`` runs Sec. 5, step 2 with the library's FP64 GPU kernels
+(:mod:`.krylov_setup`): one GMRES run for the single polynomials and p_in,
+GMRES on A p_in(A) for p_out, PP-Arnoldi plus the Sec. 4 acceptance rule
+for the eigenpairs.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import krylov_setup
+from . import mpmc as G
+from . import synth
+
+
+@dataclass(frozen=True)
+class Workload:
+    key: str
+    dims: tuple
+    links: str
+    gauge_seed: int
+    eps: float
+    kappa: float
+    levels: tuple            # ("single", d) or ("composite", m_in, m_out)
+    k: int                   # deflation eigenpairs
+    nsamples: int            # Z4 noise vectors per level
+    noise_seed: int
+    setup_seed: int
+    arnoldi_m: int = 0       # PP-Arnoldi steps for the eigenpairs
+    ndefinit: int = 0        # Ritz values considered (Sec. 4)
+    block: int = 64          # right-hand sides per launch
+
+    @property
+    def V(self):
+        lx, ly, lz, lt = self.dims
+        return lx * ly * lz * lt
+
+    @property
+    def n(self):
+        return 12 * self.V
+
+    def degrees(self):
+        out = []
+        for lv in self.levels:
+            out.append(lv[1] if lv[0] == "single" else lv[1] * lv[2] - 1)
+        return out
+
+    def applies_per_step(self):
+        """Noise-vector polynomial applications in one pass over all levels."""
+        L = len(self.levels)
+        return self.nsamples * (2 * (L - 1) + 1)
+
+    def matvecs_per_step(self):
+        mv = []
+        for lv in self.levels:
+            mv.append(lv[1] if lv[0] == "single" else lv[1] * lv[2] - 1)
+        L = len(mv)
+        return self.nsamples * sum(mv[l] + (mv[l + 1] if l + 1 < L else 0) for l in range(L))
+
+    def describe(self):
+        lx, ly, lz, lt = self.dims
+        lat = f"{lx}x{ly}x{lz}x{lt}"
+        lv = []
+        for x in self.levels:
+            lv.append(f"deg{x[1]}" if x[0] == "single" else f"composite{x[2]}x{x[1]}=deg{x[1] * x[2] - 1}")
+        return (f"Wilson-Dirac {lat} {self.links} eps={self.eps} kappa={self.kappa}; levels "
+                f"[{', '.join(lv)}]; {self.k} deflation eigenpairs; {self.nsamples} Z4 noises/level")
+
+
+WORKLOADS = {
+    # the small plain FP64 case: one degree-40 polynomial on a 4^4 Haar field
+    "4^4": Workload("4^4", (4, 4, 4, 4), "haar", 0, 0.0, 0.12, (("single", 40),), 0, 200, 1001, 2001,
+                    block=40),
+    # the headline multipolynomial case: 8^4, three levels, 50 eigenpairs, 512 noises/level
+    "8^4": Workload("8^4", (8, 8, 8, 8), "near_identity", 1, 0.3, 0.123,
+                    (("composite", 10, 20), ("single", 50), ("single", 10)), 50, 512, 1002, 2002,
+                    arnoldi_m=320, ndefinit=130, block=512),
+    "16^3x32": Workload("16^3x32", (16, 16, 16, 32), "near_identity", 2, 0.25, 0.1235,
+                        (("composite", 20, 30), ("single", 100), ("single", 16)), 200, 256, 1003, 2003,
+                        arnoldi_m=400, ndefinit=260, block=32),
+}
+
+
+def get(key):
+    if key not in WORKLOADS:
+        raise KeyError(f"unknown workload {key!r}; choose from {sorted(WORKLOADS)}")
+    return WORKLOADS[key]
+
+
+def gauge(wl):
+    return synth.gauge_field(wl.dims, wl.links, wl.gauge_seed, wl.eps)
+
+
+def setup(h64, wl, log=None):
+    """Polynomials [(kind, roots, outer)] and deflation (Z n x k, lam, pair) for a workload."""
+    S = krylov_setup.Setup(h64)
+    v0 = synth.random_unit_vector(wl.n, wl.setup_seed)
+    singles = [lv[1] for lv in wl.levels if lv[0] == "single"]
+    inners = [lv[1] - 1 for lv in wl.levels if lv[0] == "composite"]
+    degs = sorted(set(singles + inners))
+    roots = dict(zip(degs, S.single_roots(v0, degs)))
+    polys = []
+    inner = None
+    for lv in wl.levels:
+        if lv[0] == "single":
+            polys.append(("single", roots[lv[1]], None))
+        else:
+            inner = roots[lv[1] - 1]
+            outer, _ = S.pp_roots(inner, v0, m_out=lv[2])
+            polys.append(("composite", inner, outer))
+    defl = None
+    if wl.k > 0:
+        pin = inner if inner is not None else roots[min(degs)]
+        lam, Z, pair = S.eigenpairs(pin, v0, wl.arnoldi_m, wl.ndefinit, kmax=wl.k)
+        if log:
+            log(f"setup: {lam.size} of {wl.ndefinit} Ritz pairs accepted (want {wl.k}); "
+                f"|lambda| in [{np.abs(lam).min():.4g}, {np.abs(lam).max():.4g}]")
+        defl = (Z, lam, pair)
+    return polys, defl
+
+
+def configure(h, polys, defl, block=None):
+    """Load a workload's polynomials and deflation into a handle."""
+    if defl is not None:
+        h.mpmc_set_deflation(*defl)
+    for i, (kind, r, o) in enumerate(polys):
+        if kind == "single":
+            h.mpmc_set_poly(i, G.SINGLE, r, leja=True)
+        else:
+            h.mpmc_set_poly(i, G.COMPOSITE, r, o, leja=True)
+    if block:
+        h.mpmc_set_block(block)

@@ -208,8 +208,9 @@ def test_trace_block_size_does_not_change_samples():
             h.mpmc_set_deflation(Z, lam, pair)
             set_polys(h, polys)
             out.append(h.mpmc_trace_levels(seed=5, nsamples=9)[2])
+    # level samples cancel terms of size ~n; summation order may differ by block
     for o in out[1:]:
-        assert np.max(np.abs(o - out[0]) / np.abs(out[0])) < 1e-12
+        assert np.max(np.abs(o - out[0])) < 1e-12 * op.n
 
 
 # ---------------------------------------------------------------- setup kernels
