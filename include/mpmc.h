@@ -259,6 +259,49 @@ MPMC_API int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* la
  * was created (the count a caller reports for its timed region). */
 MPMC_API long long mpmc_launch_count(mpmc_handle h);
 
+/*
+ * mpmc_trace_poly_noalloc: Hutchinson samples s_j = b_j^H p(A) b_j of one
+ * polynomial, j = first .. first+nsamples-1 (Z4 noise of level id `level`,
+ * same bits as mpmc_noise), computed without allocating any device memory.
+ * The paper has no counterpart: this is a deployment variant of the
+ * single-polynomial trace of mpmc_trace_levels (same kernels, FP64).
+ *
+ * Who it is for: callers that cannot call cudaMalloc -- an application whose
+ * framework owns the whole GPU through its own caching allocator, or code on a
+ * latency-critical path where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  The call makes no cudaMalloc, cudaFree or other allocating
+ * call and needs no handle.
+ *
+ * All intermediates (links in kernel layout, two chain vectors, FP64
+ * accumulators, samples) live in one file-scope device array of
+ * MPMC_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits.  Noise is processed in blocks of at most 64
+ * vectors, narrowed until the block fits; a lattice whose single-vector
+ * working set does not fit, 2*12*V*16 + 36*V*16 (+ 36*V*16 for host links)
+ * bytes plus a few KB, is rejected with MPMC_EINVAL before any GPU work.
+ *
+ * Arguments: dims, kappa, bc_t as in mpmc_create; links in the mpmc_create
+ * layout; roots: nroots complex values used in the given order (no Leja
+ * reordering); samples: nsamples complex outputs.  on_device != 0: links and
+ * samples are device pointers and the call is asynchronous on `stream`;
+ * otherwise both are host pointers and the call synchronises `stream`.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current); make that
+ * first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind (accumulators are cleared at the start of each
+ * call): calls that overlap on the GPU -- from different streams or host
+ * threads -- race on it and must be serialised by the caller.
+ * Errors: EINVAL (arguments, or the lattice exceeds the array), ENONFINITE
+ * (a zero or non-finite root), ENOTSUP (device index >= 128), ECUDA.
+ */
+#define MPMC_NOALLOC_SCRATCH_BYTES (32u << 20)
+MPMC_API int mpmc_trace_poly_noalloc(const int dims[4], const double* links, double kappa, int bc_t,
+                                     const double* roots, int nroots, uint64_t seed, int level,
+                                     int first, int nsamples, double* samples, int on_device,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

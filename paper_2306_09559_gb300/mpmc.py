@@ -56,9 +56,14 @@ _SIGS = {
     "mpmc_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mpmc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "mpmc_trace_poly_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.c_void_p]),
 }
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def exported_symbols():
@@ -271,3 +276,31 @@ class Handle:
         self._check(self._L.mpmc_profile_read(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
                     "mpmc_profile_read")
         return ms.value, n.value, b.value
+
+
+def mpmc_trace_poly_noalloc(links, kappa, roots, seed, level, first, nsamples, out=None, bc_t=1, stream=None):
+    """Samples b_j^H p(A) b_j without any device allocation inside the library.
+
+    links: host complex128 array (4, Lt, Lz, Ly, Lx, 3, 3) or a CUDA tensor of
+    the same layout; out: None (host result) or a CUDA complex128 tensor of
+    nsamples entries (then links must be on the device too and the call is
+    asynchronous on `stream`).  Returns the samples (host array or `out`).
+    """
+    L = lib()
+    lt, lz, ly, lx = links.shape[1:5]
+    dims = (ctypes.c_int * 4)(lx, ly, lz, lt)
+    r = _c128(roots)
+    on_dev = 1 if out is not None else 0
+    if on_dev:
+        res = out
+        lk = links
+    else:
+        res = np.zeros(nsamples, dtype=np.complex128)
+        lk = _c128(links)
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = L.mpmc_trace_poly_noalloc(dims, _ptr(lk), float(kappa), int(bc_t), _ptr(r), r.size, ctypes.c_uint64(seed),
+                                   int(level), int(first), int(nsamples), _ptr(res), on_dev,
+                                   ctypes.c_void_p(raw) if raw else None)
+    if rc != MPMC_OK:
+        raise MpmcError(rc, "mpmc_trace_poly_noalloc: " + L.mpmc_strerror(rc).decode())
+    return res
