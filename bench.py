@@ -259,6 +259,7 @@ def gpu_arm(args):
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         for k in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -266,6 +267,7 @@ def gpu_arm(args):
             results.append(one(hm, first))
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
     launches = hm.mpmc_launch_count() - l0
     st_ms, st_n, st_bytes = hm.mpmc_profile_read(G.PROF_STENCIL)
