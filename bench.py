@@ -232,7 +232,6 @@ def gpu_arm(args):
     from paper_2306_09559_gb300 import mpmc as G
     build.build()
     wl = workloads.get(args.workload)
-    block = args.block or wl.block
     U = workloads.gauge(wl)
     t0 = time.perf_counter()
     h64 = G.Handle(U, wl.kappa, G.FP64)
@@ -242,7 +241,11 @@ def gpu_arm(args):
     hm = G.Handle(U, wl.kappa, prec)
     stream = torch.cuda.Stream()
     hm.mpmc_set_stream(stream)
-    workloads.configure(hm, polys, defl, block)
+    workloads.configure(hm, polys, defl, args.block or None)
+    if not args.block:
+        hm.mpmc_autotune(wl.nsamples)          # block width and launch shape for this lattice
+    launch = hm.mpmc_get_launch()
+    block = launch["nb"]
     first = rank * wl.nsamples           # weak scaling: each rank draws its own noise indices
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
@@ -323,7 +326,8 @@ def gpu_arm(args):
     # ---------------------------------------------------------- FP64 path at equal trace error
     fp64 = None
     if not args.no_fp64 and prec != G.FP64:
-        workloads.configure(h64, polys, defl, block)
+        workloads.configure(h64, polys, defl, None)
+        h64.mpmc_autotune(min(wl.nsamples, 128), steps=2)
         s64 = torch.cuda.Stream()
         h64.mpmc_set_stream(s64)
         one(h64, first)
@@ -381,7 +385,7 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": wl.describe(), "lattice": "x".join(map(str, wl.dims)),
                        "noises_per_level": wl.nsamples, "levels": [list(x) for x in wl.levels],
-                       "deflation_k": wl.k, "nrhs_per_launch": block, "l2": "flushed before every step (256 MB write)",
+                       "deflation_k": wl.k, "nrhs_per_launch": block, "launch_shape": launch, "l2": "flushed before every step (256 MB write)",
                        "parallelism": f"noise sharding x{world}", "matvecs_per_step": wl.matvecs_per_step(),
                        "setup_s": t_setup},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,

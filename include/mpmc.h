@@ -260,6 +260,21 @@ MPMC_API int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* la
 MPMC_API long long mpmc_launch_count(mpmc_handle h);
 
 /*
+ * Launch shape of the stencil kernels (performance only; results do not
+ * depend on it beyond FP rounding order of the per-site sums):
+ * R = right-hand sides per thread (1 or 2), bx = threads along the
+ * right-hand sides per CTA (power of two <= 256), sl = sites per thread.
+ * 0 selects the default (1, 64, 1).  mpmc_get_launch reports the current
+ * shape and block width.  mpmc_autotune times short noise-started chains of
+ * `steps` fused steps (the trace-mode kernel) for block widths up to max_nb
+ * and the shapes above on this handle's lattice and precision, and keeps
+ * the fastest per site and right-hand side (block width as mpmc_set_block).
+ */
+MPMC_API int mpmc_set_launch(mpmc_handle h, int R, int bx, int sl);
+MPMC_API int mpmc_get_launch(mpmc_handle h, int* nb, int* R, int* bx, int* sl);
+MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
+
+/*
  * mpmc_trace_poly_noalloc: Hutchinson samples s_j = b_j^H p(A) b_j of one
  * polynomial, j = first .. first+nsamples-1 (Z4 noise of level id `level`,
  * same bits as mpmc_noise), computed without allocating any device memory.

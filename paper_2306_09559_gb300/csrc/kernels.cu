@@ -34,119 +34,6 @@ Lattice make_lat(const Geom& g) {
     return L;
 }
 
-// Block reduction of a per-thread complex value over threadIdx.y (fixed
-// order), then acc[blockIdx.x][col] += w * sum by the threadIdx.y == 0 row.
-template <class T>
-__device__ __forceinline__ void cta_dot_accumulate(cplx<T> v, int col, bool colok, int nb, const double (&w)[2],
-                                                   double2* acc) {
-    __shared__ double2 red[256];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    red[tid] = make_double2((double)v.re, (double)v.im);
-    __syncthreads();
-    if (threadIdx.y == 0 && colok) {
-        double sr = 0.0, si = 0.0;
-        for (int yy = 0; yy < (int)blockDim.y; ++yy) {
-            const double2 q = red[yy * blockDim.x + threadIdx.x];
-            sr += q.x;
-            si += q.y;
-        }
-        double2* pa = acc + (size_t)blockIdx.x * nb + col;
-        double2 cur = *pa;
-        cur.x += w[0] * sr - w[1] * si;
-        cur.y += w[0] * si + w[1] * sr;
-        *pa = cur;
-    }
-}
-
-// ------------------------------------------------------------------ step
-template <class S, bool NOISE_IN, bool DOT, int YMODE>
-__global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
-                                              int nb, NoiseKey nk, int sl) {
-    using T = typename Math<S>::T;
-    const int col = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool colok = col < nb;
-    const cplx<T> ca = cdv<T>(a.a), cc = cdv<T>(a.c), cya = cdv<T>(a.ya), cyb = cdv<T>(a.yb);
-    cplx<T> dsum = cz<T>();
-    const int base = blockIdx.x * blockDim.y * sl;
-    for (int it = 0; it < sl; ++it) {
-        const int site = base + it * blockDim.y + threadIdx.y;
-        if (site >= L.V || !colok) continue;
-        cplx<T> hw[12], own[12];
-        if (NOISE_IN) {
-            NoiseSource<T> src{nk};
-            wilson_hopping(L, U, src, site, col, hw);
-            src.get(site, col, own);
-        } else {
-            MemSource<S> src{reinterpret_cast<const S*>(a.in), nb};
-            wilson_hopping(L, U, src, site, col, hw);
-            src.get(site, col, own);
-        }
-        const size_t off = ((size_t)site * 12 * nb + col) * 2;
-        S* po = reinterpret_cast<S*>(a.out) + off;
-        cplx<T> out[12];
-#pragma unroll
-        for (int e = 0; e < 12; ++e) {
-            out[e] = mul(ca, own[e]) + mul(cc, hw[e]);
-            st(po + (size_t)e * nb * 2, out[e]);
-        }
-        if (YMODE == 1) {
-            S* py = reinterpret_cast<S*>(a.y) + off;
-#pragma unroll
-            for (int e = 0; e < 12; ++e) st(py + (size_t)e * nb * 2, mul(cya, own[e]) + mul(cyb, out[e]));
-        } else if (YMODE == 2) {
-            S* py = reinterpret_cast<S*>(a.y) + off;
-#pragma unroll
-            for (int e = 0; e < 12; ++e) {
-                const cplx<T> yv = ld(py + (size_t)e * nb * 2);
-                st(py + (size_t)e * nb * 2, yv + mul(cyb, out[e]));
-            }
-        }
-        if (DOT) {
-            const uint32_t w = z4_word(nk, site, col);
-#pragma unroll
-            for (int e = 0; e < 12; ++e) dsum = dsum + z4_conj_mul<T>(w >> (2 * e), out[e]);
-        }
-    }
-    if (DOT) cta_dot_accumulate(dsum, col, colok, nb, a.dot_w, a.acc);
-}
-
-// ------------------------------------------------------------------ outer
-template <class S, bool DOT>
-__global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
-                                               int nb, NoiseKey nk, int sl) {
-    using T = typename Math<S>::T;
-    const int col = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool colok = col < nb;
-    const cplx<T> ca = cdv<T>(a.a), cc = cdv<T>(a.c), cb = cdv<T>(a.beta), cg = cdv<T>(a.gamma);
-    const cplx<T> c1b = {T(1.0 - a.beta[0]), T(-a.beta[1])};
-    cplx<T> dsum = cz<T>();
-    const int base = blockIdx.x * blockDim.y * sl;
-    for (int it = 0; it < sl; ++it) {
-        const int site = base + it * blockDim.y + threadIdx.y;
-        if (site >= L.V || !colok) continue;
-        cplx<T> hw[12], own[12];
-        MemSource<S> src{reinterpret_cast<const S*>(a.in), nb};
-        wilson_hopping(L, U, src, site, col, hw);
-        src.get(site, col, own);
-        const size_t off = ((size_t)site * 12 * nb + col) * 2;
-        const S* pw = reinterpret_cast<const S*>(a.w) + off;
-        S* pwo = reinterpret_cast<S*>(a.wout) + off;
-        S* py = reinterpret_cast<S*>(a.y) + off;
-        uint32_t wq = 0;
-        if (DOT) wq = z4_word(nk, site, col);
-#pragma unroll
-        for (int e = 0; e < 12; ++e) {
-            const cplx<T> t = mul(ca, own[e]) + mul(cc, hw[e]);
-            const cplx<T> wn = mul(c1b, ld(pw + (size_t)e * nb * 2)) + mul(cb, t);
-            st(pwo + (size_t)e * nb * 2, wn);
-            const cplx<T> yn = ld(py + (size_t)e * nb * 2) + mul(cg, wn);
-            st(py + (size_t)e * nb * 2, yn);
-            if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), yn);
-        }
-    }
-    if (DOT) cta_dot_accumulate(dsum, col, colok, nb, a.dot_w, a.acc);
-}
-
 // ------------------------------------------------------------------ elementwise
 template <class S>
 __global__ void k_fill_noise(int V, int nb, NoiseKey nk, double sre, double sim, S* out) {
@@ -231,15 +118,36 @@ __global__ void k_convert(size_t n, const double* __restrict__ src, T* dst) {
 }
 
 // ------------------------------------------------------------------ finalize
-__global__ void k_finalize(int ncta, int nb, int nvalid, const double2* __restrict__ acc_hi,
-                           const double2* __restrict__ acc_lo, double2 chi, double2 clo,
-                           const double2* __restrict__ dterm, double2* samples, double2* hi, double2* lo) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= nvalid) return;
-    double2 h = chi, l = clo;
-    for (int b = 0; b < ncta; ++b) h = cadd(h, acc_hi[(size_t)b * nb + col]);
-    if (acc_lo)
-        for (int b = 0; b < ncta; ++b) l = cadd(l, acc_lo[(size_t)b * nb + col]);
+// One CTA per 32 columns; the accumulator rows are split into FIN_RG
+// contiguous chunks summed in order, then the chunk sums are added in order:
+// a fixed summation order independent of scheduling.
+constexpr int FIN_RG = 16;
+
+__global__ void __launch_bounds__(32 * FIN_RG) k_finalize(int ncta, int nb, int nvalid,
+                                                          const double2* __restrict__ acc_hi,
+                                                          const double2* __restrict__ acc_lo, double2 chi, double2 clo,
+                                                          const double2* __restrict__ dterm, double2* samples,
+                                                          double2* hi, double2* lo) {
+    __shared__ double2 red[2][FIN_RG][32];
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int chunk = (ncta + FIN_RG - 1) / FIN_RG;
+    const int b0 = threadIdx.y * chunk, b1 = min(ncta, b0 + chunk);
+    double2 h = make_double2(0, 0), l = make_double2(0, 0);
+    if (col < nvalid) {
+        for (int b = b0; b < b1; ++b) h = cadd(h, acc_hi[(size_t)b * nb + col]);
+        if (acc_lo)
+            for (int b = b0; b < b1; ++b) l = cadd(l, acc_lo[(size_t)b * nb + col]);
+    }
+    red[0][threadIdx.y][threadIdx.x] = h;
+    red[1][threadIdx.y][threadIdx.x] = l;
+    __syncthreads();
+    if (threadIdx.y != 0 || col >= nvalid) return;
+    h = chi;
+    l = clo;
+    for (int g = 0; g < FIN_RG; ++g) {
+        h = cadd(h, red[0][g][threadIdx.x]);
+        l = cadd(l, red[1][g][threadIdx.x]);
+    }
     double2 s = make_double2(h.x - l.x, h.y - l.y);
     if (dterm) s = make_double2(s.x - dterm[col].x, s.y - dterm[col].y);
     samples[col] = s;
@@ -439,66 +347,42 @@ inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t)
 }  // namespace
 
 // ================================================================== host side
-LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl) {
+LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R) {
     LaunchCfg c;
-    c.bx = std::min(nb, bx_max);
+    c.R = (R == 2 && nb % 2 == 0) ? 2 : 1;
+    const int groups = nb / c.R;                        // column groups of R
+    c.bx = std::min(groups, bx_max);
     c.by = std::max(1, 256 / c.bx);
     c.sl = std::max(1, sl);
     c.gx = (g.V + c.by * c.sl - 1) / (c.by * c.sl);   // site blocks (x: no 65535 limit)
-    c.gy = (nb + c.bx - 1) / c.bx;                     // column blocks
+    c.gy = (groups + c.bx - 1) / c.bx;                 // column blocks
     return c;
 }
 
-template <class S>
-static void step_dispatch(const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a,
-                          const LaunchCfg& c, cudaStream_t s) {
-    using T = typename Math<S>::T;
-    const dim3 grid(c.gx, c.gy), block(c.bx, c.by);
-    const Lattice L = make_lat(g);
-    const NoiseKey nk = make_key(ns);
-    const T* U = reinterpret_cast<const T*>(links);
-    const bool noise = (a.in == nullptr);
-#define MPMC_STEP(NI, D, Y) k_step<S, NI, D, Y><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl)
-    if (noise) {
-        if (a.dot) {
-            if (a.ymode == 0) MPMC_STEP(true, true, 0); else if (a.ymode == 1) MPMC_STEP(true, true, 1); else MPMC_STEP(true, true, 2);
-        } else {
-            if (a.ymode == 0) MPMC_STEP(true, false, 0); else if (a.ymode == 1) MPMC_STEP(true, false, 1); else MPMC_STEP(true, false, 2);
-        }
-    } else {
-        if (a.dot) {
-            if (a.ymode == 0) MPMC_STEP(false, true, 0); else if (a.ymode == 1) MPMC_STEP(false, true, 1); else MPMC_STEP(false, true, 2);
-        } else {
-            if (a.ymode == 0) MPMC_STEP(false, false, 0); else if (a.ymode == 1) MPMC_STEP(false, false, 1); else MPMC_STEP(false, false, 2);
-        }
-    }
-#undef MPMC_STEP
-}
-
-void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a,
+void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a0,
                  const LaunchCfg& c, cudaStream_t s) {
-    if (storage == ST_F64) step_dispatch<double>(g, links, nb, ns, a, c, s);
-    else if (storage == ST_F32) step_dispatch<float>(g, links, nb, ns, a, c, s);
-    else step_dispatch<__nv_bfloat16>(g, links, nb, ns, a, c, s);
+    StepArgs a = a0;
+    for (int i = 0; i < 2; ++i) {
+        a.af[i] = (float)a.a[i]; a.cf[i] = (float)a.c[i];
+        a.yaf[i] = (float)a.ya[i]; a.ybf[i] = (float)a.yb[i];
+    }
+    if (storage == ST_F64) step_f64(g, links, nb, ns, a, c, s);
+    else if (storage == ST_F32) step_f32(g, links, nb, ns, a, c, s);
+    else step_bf16(g, links, nb, ns, a, c, s);
 }
 
-template <class S>
-static void outer_dispatch(const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a,
-                           const LaunchCfg& c, cudaStream_t s) {
-    using T = typename Math<S>::T;
-    const dim3 grid(c.gx, c.gy), block(c.bx, c.by);
-    const Lattice L = make_lat(g);
-    const NoiseKey nk = make_key(ns);
-    const T* U = reinterpret_cast<const T*>(links);
-    if (a.dot) k_outer<S, true><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl);
-    else k_outer<S, false><<<grid, block, 0, s>>>(a, L, U, nb, nk, c.sl);
-}
-
-void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a,
+void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a0,
                   const LaunchCfg& c, cudaStream_t s) {
-    if (storage == ST_F64) outer_dispatch<double>(g, links, nb, ns, a, c, s);
-    else if (storage == ST_F32) outer_dispatch<float>(g, links, nb, ns, a, c, s);
-    else outer_dispatch<__nv_bfloat16>(g, links, nb, ns, a, c, s);
+    OuterArgs a = a0;
+    a.omb[0] = 1.0 - a.beta[0];
+    a.omb[1] = -a.beta[1];
+    for (int i = 0; i < 2; ++i) {
+        a.af[i] = (float)a.a[i]; a.cf[i] = (float)a.c[i];
+        a.betaf[i] = (float)a.beta[i]; a.gammaf[i] = (float)a.gamma[i]; a.ombf[i] = (float)a.omb[i];
+    }
+    if (storage == ST_F64) outer_f64(g, links, nb, ns, a, c, s);
+    else if (storage == ST_F32) outer_f32(g, links, nb, ns, a, c, s);
+    else outer_bf16(g, links, nb, ns, a, c, s);
 }
 
 void launch_fill_noise(int storage, const Geom& g, int nb, const NoiseSpec& ns, const double sc[2], void* out,
@@ -551,8 +435,9 @@ void launch_convert_vectors(int storage, size_t ncplx, const double* src, void* 
 void launch_finalize(int ncta, int nb, int nvalid, const double2* acc_hi, const double2* acc_lo, const double c_hi[2],
                      const double c_lo[2], const double2* dterm, double2* samples, double2* hi, double2* lo,
                      cudaStream_t s) {
-    k_finalize<<<blocks_for(nvalid, 128), 128, 0, s>>>(ncta, nb, nvalid, acc_hi, acc_lo, make_double2(c_hi[0], c_hi[1]),
-                                                      make_double2(c_lo[0], c_lo[1]), dterm, samples, hi, lo);
+    k_finalize<<<blocks_for(nvalid, 32), dim3(32, FIN_RG), 0, s>>>(ncta, nb, nvalid, acc_hi, acc_lo,
+                                                                    make_double2(c_hi[0], c_hi[1]),
+                                                                    make_double2(c_lo[0], c_lo[1]), dterm, samples, hi, lo);
 }
 
 int defl_nsplit(int V) { return std::max(1, std::min(64, V / 128)); }

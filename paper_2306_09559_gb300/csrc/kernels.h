@@ -32,6 +32,7 @@ struct StepArgs {
     double a[2], c[2], ya[2], yb[2];
     double dot_w[2];
     double2* acc;
+    float af[2], cf[2], yaf[2], ybf[2];   // the same coefficients in FP32 (filled by launch_step)
 };
 
 // Last inner step of a composite outer step (Sec. 3.2):
@@ -47,13 +48,25 @@ struct OuterArgs {
     bool dot;
     double dot_w[2];
     double2* acc;
+    double omb[2];                                   // 1 - beta (filled by launch_outer)
+    float af[2], cf[2], betaf[2], gammaf[2], ombf[2];
 };
 
 struct LaunchCfg {
     int bx, by, sl, gx, gy;   // block (bx, by), site loop sl, grid (gx, gy)
+    int R;                    // right-hand sides per thread (1 or 2)
 };
 
-LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl);
+// bx: threads per CTA along the columns (each handles R columns), 256/bx sites per CTA
+LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R = 1);
+
+// per-storage stencil launchers (stencil_f64.cu, stencil_f32.cu, stencil_bf16.cu)
+void step_f64(const Geom&, const void*, int, const NoiseSpec&, const StepArgs&, const LaunchCfg&, cudaStream_t);
+void step_f32(const Geom&, const void*, int, const NoiseSpec&, const StepArgs&, const LaunchCfg&, cudaStream_t);
+void step_bf16(const Geom&, const void*, int, const NoiseSpec&, const StepArgs&, const LaunchCfg&, cudaStream_t);
+void outer_f64(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
+void outer_f32(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
+void outer_bf16(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                  const StepArgs& a, const LaunchCfg& cfg, cudaStream_t s);

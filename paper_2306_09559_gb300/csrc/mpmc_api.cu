@@ -36,6 +36,7 @@ struct Workspace {
     double2* acc_hi = nullptr;
     double2* acc_lo = nullptr;
     int acc_rows = 0;
+    size_t acc_cap = 0;       // accumulator entries allocated per buffer
     LaunchCfg cfg{};
 };
 
@@ -73,6 +74,7 @@ struct mpmc_ctx {
     int defl_nb = 0;
     // work
     int nb_user = 0;
+    int tune_R = 1, tune_bx = 64, tune_sl = 1;   // launch shape of the stencil kernels
     Workspace ws, ws64;
     double2* samples = nullptr;
     size_t samples_cap = 0;
@@ -148,23 +150,37 @@ void free_ws(Workspace& w) {
     dev_free(w.x);
     dev_free(w.acc_hi);
     dev_free(w.acc_lo);
+    w.acc_cap = 0;
     w.nb = 0;
     w.storage = -1;
 }
 
+// Launch shape for the workspace's block; grows the accumulators if needed.
+int set_cfg(mpmc_ctx* h, Workspace& w) {
+    w.cfg = chain_config(h->g, w.nb, h->tune_bx, h->tune_sl, h->tune_R);
+    w.acc_rows = w.cfg.gx;   // one accumulator row per site block
+    const size_t need = (size_t)w.acc_rows * w.nb;
+    if (need > w.acc_cap) {
+        dev_free(w.acc_hi);
+        dev_free(w.acc_lo);
+        w.acc_cap = 0;
+        if (int rc = dev_alloc(h, &w.acc_hi, sizeof(double2) * need)) return rc;
+        if (int rc = dev_alloc(h, &w.acc_lo, sizeof(double2) * need)) return rc;
+        w.acc_cap = need;
+    }
+    return MPMC_OK;
+}
+
 int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
-    if (w.storage == storage && w.nb == nb) return MPMC_OK;
+    if (w.storage == storage && w.nb == nb) return set_cfg(h, w);
     free_ws(w);
+    w.acc_cap = 0;
     const size_t vb = (size_t)h->g.V * 12 * nb * storage_bytes(storage);
     for (auto& p : w.w)
         if (int rc = dev_alloc(h, &p, vb)) return rc;
     if (int rc = dev_alloc(h, &w.y, vb)) return rc;
     if (int rc = dev_alloc(h, &w.r, vb)) return rc;
     if (int rc = dev_alloc(h, &w.x, vb)) return rc;
-    w.cfg = chain_config(h->g, nb, 64, 1);
-    w.acc_rows = w.cfg.gx;   // one accumulator row per site block
-    if (int rc = dev_alloc(h, &w.acc_hi, sizeof(double2) * (size_t)w.acc_rows * nb)) return rc;
-    if (int rc = dev_alloc(h, &w.acc_lo, sizeof(double2) * (size_t)w.acc_rows * nb)) return rc;
     // padding columns must hold finite values: clear everything once
     for (auto& p : w.w) CK(cudaMemsetAsync(p, 0, vb, h->stream));
     CK(cudaMemsetAsync(w.y, 0, vb, h->stream));
@@ -173,7 +189,7 @@ int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
     w.storage = storage;
     w.nb = nb;
     w.V = h->g.V;
-    return MPMC_OK;
+    return set_cfg(h, w);
 }
 
 const void* links_for(const mpmc_ctx* h, int storage) { return storage == ST_F64 ? h->links64 : h->links32; }
@@ -1105,6 +1121,88 @@ int mpmc_set_links(mpmc_handle h, const double* links) {
     }
     CK(cudaStreamSynchronize(h->stream));
     return MPMC_OK;
+}
+
+int mpmc_set_launch(mpmc_handle h, int R, int bx, int sl) {
+    if (!h) return MPMC_EINVAL;
+    if (R < 0 || R > 2 || bx < 0 || bx > 256 || (bx & (bx - 1)) || sl < 0 || sl > 16)
+        return fail(h, MPMC_EINVAL, "launch shape out of range");
+    h->tune_R = R ? R : 1;
+    h->tune_bx = bx ? bx : 64;
+    h->tune_sl = sl ? sl : 1;
+    return MPMC_OK;
+}
+
+int mpmc_get_launch(mpmc_handle h, int* nb, int* R, int* bx, int* sl) {
+    if (!h) return MPMC_EINVAL;
+    if (nb) *nb = default_nb(h);
+    if (R) *R = h->tune_R;
+    if (bx) *bx = h->tune_bx;
+    if (sl) *sl = h->tune_sl;
+    return MPMC_OK;
+}
+
+int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
+    if (!h) return MPMC_EINVAL;
+    if (max_nb < 1 || max_nb > MPMC_MAX_BLOCK) return fail(h, MPMC_EINVAL, "max_nb out of range");
+    if (steps < 1) steps = 6;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = INFINITY;
+    int bnb = 0, bR = 1, bbx = 64, bsl = 1;
+    const int nbs[] = {16, 32, 64, 128, 256, 512, 1024};
+    const int bxs[] = {32, 64};
+    const int sls[] = {1, 2};
+    const NoiseSpec ns{0x5eedULL, 0, 0};
+    int rc = MPMC_OK;
+    for (int nb : nbs) {
+        if (nb > max_nb) break;
+        // the six work vectors of a block must stay within ~24 GB
+        if ((size_t)h->g.V * 12 * storage_bytes(h->storage) * 7 * nb > ((size_t)24 << 30)) break;
+        for (int R = 1; R <= 2 && !rc; ++R)
+            for (int bx : bxs)
+                for (int sl : sls) {
+                    if (nb / R < bx && bx != bxs[0]) continue;
+                    h->tune_R = R; h->tune_bx = bx; h->tune_sl = sl;
+                    if ((rc = ensure_ws(h, h->ws, h->storage, nb))) break;
+                    Workspace& ws = h->ws;
+                    auto chain = [&]() -> int {
+                        for (int j = 0; j < steps; ++j) {
+                            StepArgs a{};
+                            a.in = j == 0 ? nullptr : ws.w[(j - 1) % 2];
+                            a.out = ws.w[j % 2];
+                            a.dot = true;
+                            setc(a.a, 0.5);
+                            setc(a.c, 0.5 * h->kappa);
+                            setc(a.dot_w, 1.0);
+                            a.acc = ws.acc_hi;
+                            launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
+                        }
+                        return cuda_check(h, cudaGetLastError(), "autotune launch");
+                    };
+                    if ((rc = chain())) break;                 // warm-up
+                    if ((rc = cuda_check(h, cudaEventRecord(e0, h->stream), "event"))) break;
+                    if ((rc = chain())) break;
+                    if ((rc = cuda_check(h, cudaEventRecord(e1, h->stream), "event"))) break;
+                    if ((rc = cuda_check(h, cudaEventSynchronize(e1), "event"))) break;
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    h->launches += 2 * steps;
+                    const double per = ms / ((double)steps * nb * h->g.V);
+                    if (per < best) { best = per; bnb = nb; bR = ws.cfg.R; bbx = bx; bsl = sl; }
+                }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (bnb == 0) return fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
+    h->nb_user = bnb;
+    h->tune_R = bR;
+    h->tune_bx = bbx;
+    h->tune_sl = bsl;
+    return ensure_ws(h, h->ws, h->storage, bnb);
 }
 
 }  // extern "C"

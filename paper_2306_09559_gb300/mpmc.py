@@ -60,6 +60,9 @@ _SIGS = {
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_int, ctypes.c_void_p]),
+    "mpmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mpmc_get_launch": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
+    "mpmc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
 }
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
@@ -262,6 +265,18 @@ class Handle:
 
     def mpmc_launch_count(self):
         return int(self._L.mpmc_launch_count(self._h))
+
+    def mpmc_set_launch(self, R=0, bx=0, sl=0):
+        self._check(self._L.mpmc_set_launch(self._h, int(R), int(bx), int(sl)), "mpmc_set_launch")
+
+    def mpmc_get_launch(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self._L.mpmc_get_launch(self._h, *[ctypes.byref(x) for x in v]), "mpmc_get_launch")
+        return dict(zip(("nb", "R", "bx", "sl"), (x.value for x in v)))
+
+    def mpmc_autotune(self, max_nb, steps=6):
+        self._check(self._L.mpmc_autotune(self._h, int(max_nb), int(steps)), "mpmc_autotune")
+        return self.mpmc_get_launch()
 
     def mpmc_set_links(self, links):
         """links: (4, Lt, Lz, Ly, Lx, 3, 3) complex128 numpy array or a pinned torch tensor of the same bytes."""

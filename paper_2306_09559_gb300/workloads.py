@@ -81,7 +81,7 @@ WORKLOADS = {
     # the headline multipolynomial case: 8^4, three levels, 50 eigenpairs, 512 noises/level
     "8^4": Workload("8^4", (8, 8, 8, 8), "near_identity", 1, 0.3, 0.123,
                     (("composite", 10, 20), ("single", 50), ("single", 10)), 50, 512, 1002, 2002,
-                    arnoldi_m=320, ndefinit=130, block=512),
+                    arnoldi_m=320, ndefinit=200, block=512),
     "16^3x32": Workload("16^3x32", (16, 16, 16, 32), "near_identity", 2, 0.25, 0.1235,
                         (("composite", 20, 30), ("single", 100), ("single", 16)), 200, 256, 1003, 2003,
                         arnoldi_m=400, ndefinit=260, block=32),

@@ -199,6 +199,35 @@ def test_trace_levels_fp32_paired_bound():
         assert np.std(d.real) <= 0.3 * np.std(ref.real) + floor, level
 
 
+@pytest.mark.parametrize("prec", [G.FP64, G.FP32])
+def test_launch_shapes_do_not_change_samples(prec):
+    op, polys, lam, Z, pair = small_setup()
+    out = []
+    shapes = [(8, 1, 64, 1), (16, 2, 32, 1), (32, 2, 64, 2), (12, 2, 32, 4), (7, 2, 32, 1), (64, 1, 32, 2)]
+    for nb, R, bx, sl in shapes:
+        with handle((4, 4, 4, 4), prec=prec) as h:
+            h.mpmc_set_block(nb)
+            h.mpmc_set_launch(R, bx, sl)
+            h.mpmc_set_deflation(Z, lam, pair)
+            set_polys(h, polys)
+            out.append(h.mpmc_trace_levels(seed=5, nsamples=30)[2])
+    tol = 1e-12 if prec == G.FP64 else 2e-6
+    for o in out[1:]:
+        assert np.max(np.abs(o - out[0])) < tol * op.n
+
+
+def test_autotune_picks_a_valid_shape():
+    op, polys, lam, Z, pair = small_setup()
+    with handle((4, 4, 4, 4), prec=G.FP32) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        set_polys(h, polys)
+        cfg = h.mpmc_autotune(64)
+        assert cfg["nb"] in (16, 32, 64) and cfg["R"] in (1, 2) and cfg["bx"] in (32, 64) and cfg["sl"] in (1, 2)
+        s = h.mpmc_trace_levels(seed=5, nsamples=20)[2]
+    ref = M.level_samples(op, polys, 2, 5, 20)
+    assert np.max(np.abs(s[2] - ref)) < 1e-5 * op.n
+
+
 def test_trace_block_size_does_not_change_samples():
     op, polys, lam, Z, pair = small_setup()
     out = []
