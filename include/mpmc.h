@@ -275,6 +275,29 @@ MPMC_API int mpmc_get_launch(mpmc_handle h, int* nb, int* R, int* bx, int* sl);
 MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
 
 /*
+ * Options.  MPMC_OPT_TENSOR_CORE_DEFLATION (default 1): on FP32 / BF16S
+ * handles, form the deflation dots of Sec. 4.1 with the tcgen05 tensor-core
+ * kernel (BF16 hi + lo split of the vectors, FP32 accumulation) instead of
+ * the CUDA-core kernel.  Both use the same stored vectors zhat = hi + lo, so
+ * the exact correction matches either way.  mpmc_get_option reports whether
+ * the tensor-core path is in use (1) or not (0).
+ */
+enum { MPMC_OPT_TENSOR_CORE_DEFLATION = 1 };
+MPMC_API int mpmc_set_option(mpmc_handle h, int option, int value);
+MPMC_API int mpmc_get_option(mpmc_handle h, int option, int* value);
+
+/*
+ * mpmc_deflation_dots: the deflation inner products of Sec. 4.1 for noise
+ * vectors first .. first+nrhs-1 of level `level`: G1[i][c] = z_i^H b_c and
+ * G2[i][c] = z_i^H gamma5 b_c (host outputs, k x nrhs complex, row i at
+ * offset 2*i*nrhs), computed by the path the handle uses in
+ * mpmc_trace_levels (tensor cores or CUDA cores), with z_i as stored.
+ * Errors: ESTATE (no deflation), EINVAL, ETIMEOUT, ECUDA.
+ */
+MPMC_API int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int first, int nrhs, double* G1,
+                                 double* G2);
+
+/*
  * mpmc_trace_poly_noalloc: Hutchinson samples s_j = b_j^H p(A) b_j of one
  * polynomial, j = first .. first+nsamples-1 (Z4 noise of level id `level`,
  * same bits as mpmc_noise), computed without allocating any device memory.

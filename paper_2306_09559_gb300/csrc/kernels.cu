@@ -456,6 +456,11 @@ void launch_defl_reduce(int k, int nb, int nsplit, const double2* part, const do
     k_defl_term<<<blocks_for(nb, 128), 128, 0, s>>>(k, nb, coef, pair, G1, G2, term);
 }
 
+void launch_defl_term(int k, int nb, const double2* coef, const int* pair, const double2* G1, const double2* G2,
+                      double2* term, cudaStream_t s) {
+    k_defl_term<<<blocks_for(nb, 128), 128, 0, s>>>(k, nb, coef, pair, G1, G2, term);
+}
+
 void launch_defl_norms(int storage, int V, int k, const void* Z, const int* pair, double2* d, cudaStream_t s) {
     if (storage == ST_F64) k_defl_norms<double><<<k, 256, 0, s>>>(V, k, (const double*)Z, pair, d);
     else k_defl_norms<float><<<k, 256, 0, s>>>(V, k, (const float*)Z, pair, d);

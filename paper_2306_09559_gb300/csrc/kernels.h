@@ -104,6 +104,19 @@ void launch_defl_dots(int storage, const Geom& g, int k, const void* Z, int nb, 
 // term[col] = sum_i coef[i] * conj(G1[i][col]) * G2[pair[i]][col]; G1, G2 written too (k x nb each)
 void launch_defl_reduce(int k, int nb, int nsplit, const double2* part, const double2* coef, const int* pair,
                         double2* G1, double2* G2, double2* term, cudaStream_t s);
+// term[col] only, from G1, G2 already formed
+void launch_defl_term(int k, int nb, const double2* coef, const int* pair, const double2* G1, const double2* G2,
+                      double2* term, cudaStream_t s);
+
+// Tensor-core deflation dots (defl_tc.cu)
+int tc_defl_layout(int V, int k, int* Mpad, int* Kpad);
+void launch_split_bf16(int V, int k, int Mpad, int Kpad, const double* z, float* zhat, void* planes, cudaStream_t s);
+bool tc_make_map(void* map, const void* planes, int Mpad, int Kpad);
+size_t tc_map_bytes();
+void tc_defl_plan(int V, int k, int nb, int* nsplit, int* kb_per_split, size_t* part_floats);
+int tc_defl_launch(const void* map, int V, int k, int nb, const NoiseSpec& ns, float* part, int nsplit,
+                   int kb_per_split, double2* G1, double2* G2, int* err, cudaStream_t s);
+
 // d[i] = z_pair[i]^H gamma5 z_i (FP64 accumulation of the stored vectors)
 void launch_defl_norms(int storage, int V, int k, const void* Z, const int* pair, double2* d, cudaStream_t s);
 // Z (math precision) from complex double host-layout vectors

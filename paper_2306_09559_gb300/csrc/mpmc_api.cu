@@ -72,6 +72,14 @@ struct mpmc_ctx {
     double2* D = nullptr;         // projection coefficients k x nb
     double2* xz = nullptr;        // b^H Z D per column
     int defl_nb = 0;
+    // tensor-core deflation dots (reduced-precision handles)
+    void* planes = nullptr;       // BF16 hi / lo planes of the deflation vectors, [2][Mpad][Kpad]
+    alignas(64) unsigned char tmap[128];
+    bool tc_ready = false;
+    int use_tc = 1;
+    float* tc_part = nullptr;
+    size_t tc_part_cap = 0;
+    int* d_err = nullptr;         // device flag set by kernels whose bounded waits expired
     // work
     int nb_user = 0;
     int tune_R = 1, tune_bx = 64, tune_sl = 1;   // launch shape of the stencil kernels
@@ -584,6 +592,10 @@ void free_deflation(mpmc_ctx* h) {
     dev_free(h->dterm);
     dev_free(h->D);
     dev_free(h->xz);
+    dev_free(h->planes);
+    dev_free(h->tc_part);
+    h->tc_part_cap = 0;
+    h->tc_ready = false;
     h->defl_nb = 0;
     h->k = 0;
     h->lam.clear();
@@ -664,6 +676,8 @@ int mpmc_create(mpmc_handle* out, const int dims[4], const double* links, double
         dev_free(staging);
         return bail(MPMC_ECUDA);
     }
+    if ((rc = dev_alloc(h, &h->d_err, sizeof(int)))) { dev_free(staging); return bail(rc); }
+    if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) { dev_free(staging); return bail(MPMC_ECUDA); }
     if ((rc = dev_alloc(h, &h->links64, nl * 16))) { dev_free(staging); return bail(rc); }
     launch_links(ST_F64, h->g.V, staging, h->links64, h->stream);
     if (h->storage != ST_F64) {
@@ -692,6 +706,7 @@ int mpmc_destroy(mpmc_handle h) {
     dev_free(h->kr_part);
     dev_free(h->kr_h);
     dev_free(h->kr_nrm);
+    dev_free(h->d_err);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own) cudaStreamDestroy(h->own);
     delete h;
@@ -789,8 +804,19 @@ int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, con
     if (int rc = ensure_io(h, ncplx)) return rc;
     CK(cudaMemcpyAsync(h->io, Z, ncplx * 16, cudaMemcpyHostToDevice, h->stream));
     if (int rc = dev_alloc(h, &h->Z, ncplx * (zst == ST_F64 ? 16 : 8))) return rc;
-    launch_convert_vectors(zst, ncplx, h->io, h->Z, h->stream);
-    LAUNCHED(1);
+    if (zst == ST_F64) {
+        launch_convert_vectors(zst, ncplx, h->io, h->Z, h->stream);
+        LAUNCHED(1);
+    } else {
+        // reduced precision: z is held as zhat = hi + lo (two BF16 terms, exact in FP32); the
+        // CUDA-core and tensor-core dots and the exact correction all use these same vectors
+        int Mpad, Kpad;
+        tc_defl_layout(h->g.V, k, &Mpad, &Kpad);
+        if (int rc = dev_alloc(h, &h->planes, (size_t)2 * Mpad * Kpad * 2)) return rc;
+        launch_split_bf16(h->g.V, k, Mpad, Kpad, h->io, reinterpret_cast<float*>(h->Z), h->planes, h->stream);
+        LAUNCHED(1);
+        h->tc_ready = tc_make_map(h->tmap, h->planes, Mpad, Kpad);
+    }
     if (int rc = dev_alloc(h, &h->d_pair, sizeof(int) * k)) return rc;
     CK(cudaMemcpyAsync(h->d_pair, pair, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
     if (int rc = dev_alloc(h, &h->d_dnorm, sizeof(double2) * k)) return rc;
@@ -935,14 +961,34 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
             if (has_lo)
                 if (int rc = chain_trace(h, ws, h->polys[l + 1], ns, nullptr, ws.acc_lo, &c_lo)) return rc;
             if (defl) {
-                if (int rc = prof_begin(h, PROF_DEFLATION, (double)h->k * nsites12(h) * (h->storage == ST_F64 ? 16 : 8)))
-                    return rc;
-                launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part,
-                                 nsplit, h->stream);
-                if (int rc = prof_end(h)) return rc;
-                launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1,
-                                   h->G2, h->dterm, h->stream);
-                LAUNCHED(3);
+                const bool tcore = h->storage != ST_F64 && h->use_tc && h->tc_ready;
+                const double zbytes = (double)h->k * nsites12(h) * (h->storage == ST_F64 ? 16 : (tcore ? 8 : 8));
+                if (int rc = prof_begin(h, PROF_DEFLATION, zbytes)) return rc;
+                if (tcore) {
+                    int tsplit, kbps;
+                    size_t pf;
+                    tc_defl_plan(h->g.V, h->k, nb, &tsplit, &kbps, &pf);
+                    if (h->tc_part_cap < pf) {
+                        dev_free(h->tc_part);
+                        h->tc_part_cap = 0;
+                        if (int rc = dev_alloc(h, &h->tc_part, pf * sizeof(float))) return rc;
+                        h->tc_part_cap = pf;
+                    }
+                    if (tc_defl_launch(h->tmap, h->g.V, h->k, nb, ns, h->tc_part, tsplit, kbps, h->G1, h->G2,
+                                       h->d_err, h->stream))
+                        return fail(h, MPMC_ECUDA, "tensor-core deflation kernel setup failed");
+                    if (int rc = prof_end(h)) return rc;
+                    launch_defl_term(h->k, nb, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1, h->G2, h->dterm,
+                                     h->stream);
+                    LAUNCHED(3);
+                } else {
+                    launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part,
+                                     nsplit, h->stream);
+                    if (int rc = prof_end(h)) return rc;
+                    launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef + (size_t)l * h->k, h->d_pair,
+                                       h->G1, h->G2, h->dterm, h->stream);
+                    LAUNCHED(3);
+                }
             }
             double chi[2], clo[2];
             setc(chi, c_hi);
@@ -957,6 +1003,14 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
     CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (int rc = prof_collect(h)) return rc;
+    {
+        int flag = 0;
+        CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            CK(cudaMemset(h->d_err, 0, sizeof(int)));
+            return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (tensor-core deflation pipeline)");
+        }
+    }
     for (size_t i = 0; i < need; ++i)
         if (!std::isfinite(hs[i].x) || !std::isfinite(hs[i].y)) return fail(h, MPMC_ENONFINITE, "non-finite sample");
     for (int l = 0; l < L; ++l) {
@@ -1203,6 +1257,70 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     h->tune_bx = bbx;
     h->tune_sl = bsl;
     return ensure_ws(h, h->ws, h->storage, bnb);
+}
+
+int mpmc_set_option(mpmc_handle h, int option, int value) {
+    if (!h) return MPMC_EINVAL;
+    switch (option) {
+        case MPMC_OPT_TENSOR_CORE_DEFLATION:
+            h->use_tc = value != 0;
+            return MPMC_OK;
+        default:
+            return fail(h, MPMC_EINVAL, "unknown option");
+    }
+}
+
+int mpmc_get_option(mpmc_handle h, int option, int* value) {
+    if (!h || !value) return MPMC_EINVAL;
+    switch (option) {
+        case MPMC_OPT_TENSOR_CORE_DEFLATION:
+            *value = (h->use_tc && h->tc_ready && h->storage != ST_F64) ? 1 : 0;
+            return MPMC_OK;
+        default:
+            return fail(h, MPMC_EINVAL, "unknown option");
+    }
+}
+
+int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int first, int nrhs, double* G1, double* G2) {
+    if (!h) return MPMC_EINVAL;
+    if (h->k == 0) return fail(h, MPMC_ESTATE, "no deflation vectors set");
+    if (nrhs < 1 || nrhs > MPMC_MAX_BLOCK || level < 0 || first < 0 || !G1 || !G2)
+        return fail(h, MPMC_EINVAL, "bad deflation_dots arguments");
+    if (int rc = ensure_defl_work(h, nrhs)) return rc;
+    const NoiseSpec ns{seed, (uint32_t)level, (uint32_t)first};
+    const bool tcore = h->storage != ST_F64 && h->use_tc && h->tc_ready;
+    if (tcore) {
+        int tsplit, kbps;
+        size_t pf;
+        tc_defl_plan(h->g.V, h->k, nrhs, &tsplit, &kbps, &pf);
+        if (h->tc_part_cap < pf) {
+            dev_free(h->tc_part);
+            h->tc_part_cap = 0;
+            if (int rc = dev_alloc(h, &h->tc_part, pf * sizeof(float))) return rc;
+            h->tc_part_cap = pf;
+        }
+        if (tc_defl_launch(h->tmap, h->g.V, h->k, nrhs, ns, h->tc_part, tsplit, kbps, h->G1, h->G2, h->d_err,
+                           h->stream))
+            return fail(h, MPMC_ECUDA, "tensor-core deflation kernel setup failed");
+        LAUNCHED(2);
+    } else {
+        const int nsplit = defl_nsplit(h->g.V);
+        launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nrhs, ns, h->defl_part, nsplit,
+                         h->stream);
+        launch_defl_reduce(h->k, nrhs, nsplit, h->defl_part, h->d_coef, h->d_pair, h->G1, h->G2, h->dterm, h->stream);
+        LAUNCHED(3);
+    }
+    const size_t cnt = (size_t)h->k * nrhs;
+    CK(cudaMemcpyAsync(G1, h->G1, cnt * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(G2, h->G2, cnt * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (tensor-core deflation pipeline)");
+    }
+    return MPMC_OK;
 }
 
 }  // extern "C"

@@ -63,7 +63,13 @@ _SIGS = {
     "mpmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mpmc_get_launch": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "mpmc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "mpmc_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "mpmc_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mpmc_deflation_dots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
 }
+
+OPT_TENSOR_CORE_DEFLATION = 1
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -277,6 +283,21 @@ class Handle:
     def mpmc_autotune(self, max_nb, steps=6):
         self._check(self._L.mpmc_autotune(self._h, int(max_nb), int(steps)), "mpmc_autotune")
         return self.mpmc_get_launch()
+
+    def mpmc_set_option(self, option, value):
+        self._check(self._L.mpmc_set_option(self._h, int(option), int(value)), "mpmc_set_option")
+
+    def mpmc_get_option(self, option):
+        v = ctypes.c_int()
+        self._check(self._L.mpmc_get_option(self._h, int(option), ctypes.byref(v)), "mpmc_get_option")
+        return v.value
+
+    def mpmc_deflation_dots(self, seed, level, first, nrhs, k):
+        G1 = np.zeros((k, nrhs), dtype=np.complex128)
+        G2 = np.zeros((k, nrhs), dtype=np.complex128)
+        self._check(self._L.mpmc_deflation_dots(self._h, ctypes.c_uint64(seed), int(level), int(first), int(nrhs),
+                                                _ptr(G1), _ptr(G2)), "mpmc_deflation_dots")
+        return G1, G2
 
     def mpmc_set_links(self, links):
         """links: (4, Lt, Lz, Ly, Lx, 3, 3) complex128 numpy array or a pinned torch tensor of the same bytes."""

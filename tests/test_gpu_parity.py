@@ -242,6 +242,65 @@ def test_trace_block_size_does_not_change_samples():
         assert np.max(np.abs(o - out[0])) < 1e-12 * op.n
 
 
+# ---------------------------------------------------------------- deflation dots
+def _zhat(Z):
+    """z rounded as the reduced-precision handles store it: hi = bf16(z), lo = bf16(z - hi)."""
+    torch = pytest.importorskip("torch")
+    Zc = np.ascontiguousarray(Z)
+    x = torch.from_numpy(Zc.view(np.float64)).float()
+    hi = x.bfloat16().float()
+    lo = (x - hi).bfloat16().float()
+    return np.ascontiguousarray((hi + lo).double().numpy()).view(np.complex128).reshape(Zc.shape)
+
+
+@pytest.mark.parametrize("nrhs", [1, 37, 64, 130])
+def test_deflation_dots_tensor_core_vs_cuda_core_vs_oracle(nrhs):
+    op, polys, lam, Z, pair = small_setup()
+    with handle((4, 4, 4, 4), prec=G.FP32) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        assert h.mpmc_get_option(G.OPT_TENSOR_CORE_DEFLATION) == 1
+        T1, T2 = h.mpmc_deflation_dots(31, 1, 7, nrhs, lam.size)
+        h.mpmc_set_option(G.OPT_TENSOR_CORE_DEFLATION, 0)
+        assert h.mpmc_get_option(G.OPT_TENSOR_CORE_DEFLATION) == 0
+        C1, C2 = h.mpmc_deflation_dots(31, 1, 7, nrhs, lam.size)
+    B = philox.z4_block(31, 1, 7, nrhs, op.n // 12)
+    Zh = _zhat(Z)
+    R1 = Zh.conj().T @ B
+    R2 = Zh.conj().T @ op.gamma5(B)
+    scale = np.max(np.abs(R1))
+    # both device paths use zhat with FP32 accumulation
+    for got in (T1, C1):
+        assert np.max(np.abs(got - R1)) < 2e-6 * scale
+    for got in (T2, C2):
+        assert np.max(np.abs(got - R2)) < 2e-6 * scale
+    # and zhat is within the BF16 hi + lo precision of z
+    assert np.max(np.abs(Z.conj().T @ B - R1)) < 1e-3 * scale
+
+
+def test_deflation_dots_fp64_path():
+    op, polys, lam, Z, pair = small_setup()
+    with handle((4, 4, 4, 4), prec=G.FP64) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        assert h.mpmc_get_option(G.OPT_TENSOR_CORE_DEFLATION) == 0
+        G1, G2 = h.mpmc_deflation_dots(5, 0, 0, 9, lam.size)
+    B = philox.z4_block(5, 0, 0, 9, op.n // 12)
+    assert np.max(np.abs(G1 - Z.conj().T @ B)) < 1e-12 * np.max(np.abs(G1))
+    assert np.max(np.abs(G2 - Z.conj().T @ op.gamma5(B))) < 1e-12 * np.max(np.abs(G2))
+
+
+def test_trace_with_tensor_core_deflation_matches_cuda_core():
+    op, polys, lam, Z, pair = small_setup()
+    out = []
+    for tcore in (1, 0):
+        with handle((4, 4, 4, 4), prec=G.FP32) as h:
+            h.mpmc_set_block(32)
+            h.mpmc_set_deflation(Z, lam, pair)
+            h.mpmc_set_option(G.OPT_TENSOR_CORE_DEFLATION, tcore)
+            set_polys(h, polys)
+            out.append(h.mpmc_trace_levels(seed=3, nsamples=40)[2])
+    assert np.max(np.abs(out[0] - out[1])) < 1e-8 * op.n
+
+
 # ---------------------------------------------------------------- setup kernels
 def test_arnoldi_fp64_matches_oracle():
     dims = (4, 4, 4, 4)
