@@ -363,9 +363,11 @@ void launch_step(int storage, const Geom& g, const void* links, int nb, const No
                  const LaunchCfg& c, cudaStream_t s) {
     StepArgs a = a0;
     for (int i = 0; i < 2; ++i) {
-        a.af[i] = (float)a.a[i]; a.cf[i] = (float)a.c[i];
-        a.yaf[i] = (float)a.ya[i]; a.ybf[i] = (float)a.yb[i];
+        a.alphaf[i] = (float)a.alpha[i];
+        a.yaf[i] = (float)a.ya[i];
+        a.ybf[i] = (float)a.yb[i];
     }
+    a.kappaf = (float)a.kappa;
     if (storage == ST_F64) step_f64(g, links, nb, ns, a, c, s);
     else if (storage == ST_F32) step_f32(g, links, nb, ns, a, c, s);
     else step_bf16(g, links, nb, ns, a, c, s);
@@ -374,12 +376,12 @@ void launch_step(int storage, const Geom& g, const void* links, int nb, const No
 void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a0,
                   const LaunchCfg& c, cudaStream_t s) {
     OuterArgs a = a0;
-    a.omb[0] = 1.0 - a.beta[0];
-    a.omb[1] = -a.beta[1];
     for (int i = 0; i < 2; ++i) {
-        a.af[i] = (float)a.a[i]; a.cf[i] = (float)a.c[i];
-        a.betaf[i] = (float)a.beta[i]; a.gammaf[i] = (float)a.gamma[i]; a.ombf[i] = (float)a.omb[i];
+        a.alphaf[i] = (float)a.alpha[i];
+        a.betaf[i] = (float)a.beta[i];
+        a.gammaf[i] = (float)a.gamma[i];
     }
+    a.kappaf = (float)a.kappa;
     if (storage == ST_F64) outer_f64(g, links, nb, ns, a, c, s);
     else if (storage == ST_F32) outer_f32(g, links, nb, ns, a, c, s);
     else outer_bf16(g, links, nb, ns, a, c, s);

@@ -18,38 +18,42 @@ struct NoiseSpec {
     uint32_t j0;
 };
 
-// One degree step of the root form (Sec. 2.3):
-//   out = a * in + c * H in      (a = 1 - 1/theta, c = kappa/theta, i.e. out = in - A in / theta)
-// optional:  y = ya * in + yb * out (ymode 1)  or  y += yb * out (ymode 2)
-// optional:  acc[cta][col] += dot_w * sum_sites b^H out   (b = the column's Z4 noise)
-// in == nullptr means "in is the noise block itself".
+// One degree step of the root form (Sec. 2.3), in the order that keeps the
+// matrix the same at every step whatever the working precision:
+//   t   = in - kappa * H in                 (t = A in)
+//   out = in - alpha * t                    (out = (I - A/theta) in, alpha = 1/theta)
+// (op_only: out = t).  Optional:  y = ya * in + yb * out (ymode 1)  or
+// y += yb * out (ymode 2);  acc[cta][col] += dot_w * sum_sites b^H out
+// (b = the column's Z4 noise).  in == nullptr means "in is the noise block".
 struct StepArgs {
     const void* in;
     void* out;
     void* y;
     int ymode;
     bool dot;
-    double a[2], c[2], ya[2], yb[2];
+    bool op_only;
+    double alpha[2], ya[2], yb[2];
     double dot_w[2];
     double2* acc;
-    float af[2], cf[2], yaf[2], ybf[2];   // the same coefficients in FP32 (filled by launch_step)
+    double kappa;
+    float alphaf[2], yaf[2], ybf[2], kappaf;   // the same in FP32 (filled by launch_step)
 };
 
 // Last inner step of a composite outer step (Sec. 3.2):
-//   t  = a * in + c * H in                    (t = pi_in(A) w, not stored)
-//   wn = (1 - beta) * w + beta * t            (wn = (I - B/eta) w, B = A p_in(A))
+//   t  = in - alpha * (in - kappa H in)       (t = pi_in(A) w, not stored)
+//   wn = w - beta * (w - t)                   (wn = (I - B/eta) w, B = A p_in(A))
 //   y += gamma * wn;  optional acc += dot_w * b^H y
 struct OuterArgs {
     const void* in;
     const void* w;
     void* wout;
     void* y;
-    double a[2], c[2], beta[2], gamma[2];
+    double alpha[2], beta[2], gamma[2];
     bool dot;
     double dot_w[2];
     double2* acc;
-    double omb[2];                                   // 1 - beta (filled by launch_outer)
-    float af[2], cf[2], betaf[2], gammaf[2], ombf[2];
+    double kappa;
+    float alphaf[2], betaf[2], gammaf[2], kappaf;
 };
 
 struct LaunchCfg {

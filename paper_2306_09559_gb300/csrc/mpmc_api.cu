@@ -325,6 +325,16 @@ int num_levels(const mpmc_ctx* h) {
 
 inline void setc(double (&d)[2], cd z) { d[0] = z.real(); d[1] = z.imag(); }
 
+// A coefficient as the kernels of a storage format apply it: reduced-precision
+// kernels use the FP32 value, so the host uses the same value wherever it
+// weights their results (dot weights, closed-form terms).  The chain then
+// applies exactly the polynomial with roots 1/rnd(1/theta) to the matrix with
+// kappa rounded once.
+inline cd rnd(int storage, cd z) {
+    if (storage == ST_F64) return z;
+    return cd((double)(float)z.real(), (double)(float)z.imag());
+}
+
 // ------------------------------------------------------------------ chains
 // Trace mode: acc += sum of weighted b^H w over all steps of p(A) applied to
 // the start block (noise when start == nullptr); *cst receives the weighted
@@ -349,9 +359,9 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             a.ymode = 0;
             a.dot = true;
             const cd al = 1.0 / th[j - 1];
-            setc(a.a, 1.0 - al);
-            setc(a.c, h->kappa * al);
-            setc(a.dot_w, 1.0 / th[j]);
+            setc(a.alpha, rnd(st, al));
+            a.kappa = h->kappa;
+            setc(a.dot_w, rnd(st, 1.0 / th[j]));
             a.acc = acc;
             if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
@@ -359,7 +369,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         return MPMC_OK;
     };
     if (p.kind == MPMC_SINGLE) {
-        if (start == nullptr) *cst = n / p.roots[0];
+        if (start == nullptr) *cst = n * rnd(st, 1.0 / p.roots[0]);
         else return fail(h, MPMC_EINVAL, "internal: single chain from a buffer in trace mode");
         return single_from(p.roots, nullptr, true);
     }
@@ -381,13 +391,13 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
     Wnxt = ws.w[3];
     {
         double s1[2];
-        setc(s1, 1.0 / eta[0]);
+        setc(s1, rnd(st, 1.0 / eta[0]));
         launch_scale(st, ncplx, Wcur, s1, ws.y, h->stream);
         LAUNCHED(1);
     }
     if (m_out == 1) {
         // y = b / eta_1; the final chain's first dot is in closed form only for noise starts
-        if (start == nullptr) *cst = n / (eta[0] * th[0]);
+        if (start == nullptr) *cst = n * rnd(st, 1.0 / eta[0]) * rnd(st, 1.0 / th[0]);
         else return fail(h, MPMC_ENOTSUP, "internal: projected composite needs at least two outer roots");
     }
     for (int k = 1; k < m_out; ++k) {
@@ -399,8 +409,8 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             a.ymode = 0;
             a.dot = false;
             const cd al = 1.0 / th[j - 1];
-            setc(a.a, 1.0 - al);
-            setc(a.c, h->kappa * al);
+            setc(a.alpha, rnd(st, al));
+            a.kappa = h->kappa;
             if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
@@ -410,12 +420,12 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         o.wout = Wnxt;
         o.y = ws.y;
         const cd al = 1.0 / th[m_in - 1];
-        setc(o.a, 1.0 - al);
-        setc(o.c, h->kappa * al);
-        setc(o.beta, 1.0 / eta[k - 1]);
-        setc(o.gamma, 1.0 / eta[k]);
+        setc(o.alpha, rnd(st, al));
+        o.kappa = h->kappa;
+        setc(o.beta, rnd(st, 1.0 / eta[k - 1]));
+        setc(o.gamma, rnd(st, 1.0 / eta[k]));
         o.dot = (k == m_out - 1);
-        setc(o.dot_w, 1.0 / th[0]);
+        setc(o.dot_w, rnd(st, 1.0 / th[0]));
         o.acc = acc;
         if (int rc = do_outer(h, ws, o, ns)) return rc;
         // never write into the caller's start buffer: alternate between w[2] and w[3]
@@ -431,9 +441,9 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         a.ymode = 0;
         a.dot = true;
         const cd al = 1.0 / th[j - 1];
-        setc(a.a, 1.0 - al);
-        setc(a.c, h->kappa * al);
-        setc(a.dot_w, 1.0 / th[j]);
+        setc(a.alpha, rnd(st, al));
+        a.kappa = h->kappa;
+        setc(a.dot_w, rnd(st, 1.0 / th[j]));
         a.acc = acc;
         if (int rc = do_step(h, ws, a, ns)) return rc;
         in = a.out;
@@ -450,7 +460,7 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
     const size_t ncplx = (size_t)h->g.V * 12 * nb;
     if (m == 1) {
         double s1[2];
-        setc(s1, 1.0 / th[0]);
+        setc(s1, rnd(st, 1.0 / th[0]));
         launch_scale(st, ncplx, in0, s1, X, h->stream);
         LAUNCHED(1);
         return MPMC_OK;
@@ -464,10 +474,10 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
         a.ymode = (j == 1) ? 1 : 2;
         a.dot = false;
         const cd al = 1.0 / th[j - 1];
-        setc(a.a, 1.0 - al);
-        setc(a.c, h->kappa * al);
-        setc(a.ya, 1.0 / th[0]);
-        setc(a.yb, 1.0 / th[j]);
+        setc(a.alpha, rnd(st, al));
+        a.kappa = h->kappa;
+        setc(a.ya, rnd(st, 1.0 / th[0]));
+        setc(a.yb, rnd(st, 1.0 / th[j]));
         if (int rc = do_step(h, ws, a, ns)) return rc;
         in = a.out;
     }
@@ -484,7 +494,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
     const int m_in = (int)th.size(), m_out = (int)eta.size();
     const size_t ncplx = (size_t)h->g.V * 12 * nb;
     double s1[2];
-    setc(s1, 1.0 / eta[0]);
+    setc(s1, rnd(st, 1.0 / eta[0]));
     launch_scale(st, ncplx, in0, s1, ws.y, h->stream);
     LAUNCHED(1);
     const void* Wcur = in0;
@@ -496,8 +506,8 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
             a.in = in;
             a.out = ws.w[(j - 1) % 2];
             const cd al = 1.0 / th[j - 1];
-            setc(a.a, 1.0 - al);
-            setc(a.c, h->kappa * al);
+            setc(a.alpha, rnd(st, al));
+            a.kappa = h->kappa;
             if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
@@ -507,10 +517,10 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
         o.wout = Wnxt;
         o.y = ws.y;
         const cd al = 1.0 / th[m_in - 1];
-        setc(o.a, 1.0 - al);
-        setc(o.c, h->kappa * al);
-        setc(o.beta, 1.0 / eta[k - 1]);
-        setc(o.gamma, 1.0 / eta[k]);
+        setc(o.alpha, rnd(st, al));
+        o.kappa = h->kappa;
+        setc(o.beta, rnd(st, 1.0 / eta[k - 1]));
+        setc(o.gamma, rnd(st, 1.0 / eta[k]));
         o.dot = false;
         if (int rc = do_outer(h, ws, o, ns)) return rc;
         Wcur = Wnxt;
@@ -524,8 +534,8 @@ int apply_A(mpmc_ctx* h, Workspace& ws, const void* in, void* out) {
     StepArgs a{};
     a.in = in;
     a.out = out;
-    setc(a.a, 1.0);
-    setc(a.c, -h->kappa);
+    a.op_only = true;
+    a.kappa = h->kappa;
     const NoiseSpec ns{0, 0, 0};
     return do_step(h, ws, a, ns);
 }
@@ -1227,8 +1237,8 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                             a.in = j == 0 ? nullptr : ws.w[(j - 1) % 2];
                             a.out = ws.w[j % 2];
                             a.dot = true;
-                            setc(a.a, 0.5);
-                            setc(a.c, 0.5 * h->kappa);
+                            setc(a.alpha, 0.5);
+                            a.kappa = h->kappa;
                             setc(a.dot_w, 1.0);
                             a.acc = ws.acc_hi;
                             launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);

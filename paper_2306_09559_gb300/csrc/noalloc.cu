@@ -134,8 +134,8 @@ extern "C" MPMC_API int mpmc_trace_poly_noalloc(const int dims[4], const double*
             a.out = w[(j - 1) % 2];
             a.ymode = 0;
             a.dot = true;
-            a.a[0] = 1.0 - al.real(); a.a[1] = -al.imag();
-            a.c[0] = kappa * al.real(); a.c[1] = kappa * al.imag();
+            a.alpha[0] = al.real(); a.alpha[1] = al.imag();
+            a.kappa = kappa;
             a.dot_w[0] = wnext.real(); a.dot_w[1] = wnext.imag();
             a.acc = acc;
             launch_step(ST_F64, g, S + p.off_links, nb, ns, a, p.cfg, st);

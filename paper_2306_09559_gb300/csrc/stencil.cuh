@@ -228,10 +228,24 @@ __device__ __forceinline__ void hopping_r(const Lattice& L, const T* __restrict_
 template <class T> struct Coef;
 template <> struct Coef<float> {
     static __device__ __forceinline__ cplx<float> get(const double (&)[2], const float (&f)[2]) { return {f[0], f[1]}; }
+    static __device__ __forceinline__ float real(double, float f) { return f; }
 };
 template <> struct Coef<double> {
     static __device__ __forceinline__ cplx<double> get(const double (&d)[2], const float (&)[2]) { return {d[0], d[1]}; }
+    static __device__ __forceinline__ double real(double d, float) { return d; }
 };
+
+// t = own - kappa * hw  (A applied), then out = own - alpha * t
+template <class T>
+__device__ __forceinline__ cplx<T> apply_A_elem(cplx<T> own, cplx<T> hw, T kappa) {
+    return {fma(-kappa, hw.re, own.re), fma(-kappa, hw.im, own.im)};
+}
+template <class T>
+__device__ __forceinline__ cplx<T> minus_alpha(cplx<T> own, cplx<T> alpha, cplx<T> t) {
+    cplx<T> o = own;
+    cmac(o, cplx<T>{-alpha.re, -alpha.im}, t);
+    return o;
+}
 
 // Reduce R per-thread partial dots over threadIdx.y in fixed order (FP64),
 // then acc[blockIdx.x][col] += w * sum.
@@ -268,7 +282,9 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typen
     using T = typename Math<S>::T;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> ca = Coef<T>::get(a.a, a.af), cc = Coef<T>::get(a.c, a.cf);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf);
+    const bool op_only = a.op_only;
     const cplx<T> cya = Coef<T>::get(a.ya, a.yaf), cyb = Coef<T>::get(a.yb, a.ybf);
     cplx<T> dsum[R];
 #pragma unroll
@@ -299,8 +315,8 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typen
             cplx<T> out[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                out[r] = cmul_f(ca, own[e][r]);
-                cmac(out[r], cc, hw[e][r]);
+                const cplx<T> t = apply_A_elem(own[e][r], hw[e][r], kap);
+                out[r] = op_only ? t : minus_alpha(own[e][r], cal, t);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), out[r]);
             }
             VecIO<S, R>::st(po + (size_t)e * nb * 2, out);
@@ -331,9 +347,9 @@ __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typ
     using T = typename Math<S>::T;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> ca = Coef<T>::get(a.a, a.af), cc = Coef<T>::get(a.c, a.cf);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf);
     const cplx<T> cb = Coef<T>::get(a.beta, a.betaf), cg = Coef<T>::get(a.gamma, a.gammaf);
-    const cplx<T> c1b = Coef<T>::get(a.omb, a.ombf);
     cplx<T> dsum[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dsum[r] = cz<T>();
@@ -360,10 +376,8 @@ __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typ
             VecIO<S, R>::ld(py + (size_t)e * nb * 2, yv);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                cplx<T> t = cmul_f(ca, own[e][r]);
-                cmac(t, cc, hw[e][r]);
-                cplx<T> wn = cmul_f(c1b, wv[r]);
-                cmac(wn, cb, t);
+                const cplx<T> t = minus_alpha(own[e][r], cal, apply_A_elem(own[e][r], hw[e][r], kap));
+                const cplx<T> wn = minus_alpha(wv[r], cb, wv[r] - t);
                 wv[r] = wn;
                 cmac(yv[r], cg, wn);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), yv[r]);
