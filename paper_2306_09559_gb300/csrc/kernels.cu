@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(32 * FIN_RG) k_finalize(int ncta, int nb, int 
                                                           const double2* __restrict__ acc_hi,
                                                           const double2* __restrict__ acc_lo, double2 chi, double2 clo,
                                                           const double2* __restrict__ dterm, double2* samples,
-                                                          double2* hi, double2* lo) {
+                                                          double2* hi, double2* lo,
+                                                          const double2* __restrict__ add_hi) {
     __shared__ double2 red[2][FIN_RG][32];
     const int col = blockIdx.x * 32 + threadIdx.x;
     const int chunk = (ncta + FIN_RG - 1) / FIN_RG;
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(32 * FIN_RG) k_finalize(int ncta, int nb, int 
     if (threadIdx.y != 0 || col >= nvalid) return;
     h = chi;
     l = clo;
+    if (add_hi) h = cadd(h, add_hi[col]);
     for (int g = 0; g < FIN_RG; ++g) {
         h = cadd(h, red[0][g][threadIdx.x]);
         l = cadd(l, red[1][g][threadIdx.x]);
@@ -436,10 +438,11 @@ void launch_convert_vectors(int storage, size_t ncplx, const double* src, void* 
 
 void launch_finalize(int ncta, int nb, int nvalid, const double2* acc_hi, const double2* acc_lo, const double c_hi[2],
                      const double c_lo[2], const double2* dterm, double2* samples, double2* hi, double2* lo,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double2* add_hi) {
     k_finalize<<<blocks_for(nvalid, 32), dim3(32, FIN_RG), 0, s>>>(ncta, nb, nvalid, acc_hi, acc_lo,
                                                                     make_double2(c_hi[0], c_hi[1]),
-                                                                    make_double2(c_lo[0], c_lo[1]), dterm, samples, hi, lo);
+                                                                    make_double2(c_lo[0], c_lo[1]), dterm, samples, hi, lo,
+                                                                    add_hi);
 }
 
 int defl_nsplit(int V) { return std::max(1, std::min(64, V / 128)); }

@@ -97,7 +97,19 @@ void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t
 // also hi/lo parts (may be null).  acc_lo/dterm may be null.
 void launch_finalize(int ncta, int nb, int nvalid, const double2* acc_hi, const double2* acc_lo,
                      const double c_hi[2], const double c_lo[2], const double2* dterm,
-                     double2* samples, double2* hi, double2* lo, cudaStream_t s);
+                     double2* samples, double2* hi, double2* lo, cudaStream_t s,
+                     const double2* add_hi = nullptr);
+
+// Projection of the projected composite polynomial (proj.cu)
+int gram_nsplit(int V);
+void launch_block_gram(int math, int V, const void* X, int kx, int sy, const void* Y, int ky, int g5, double2* part,
+                       int nsplit, double2* out, cudaStream_t s);
+void launch_proj_coef(int k, int nb, const int* pair, const double2* inv_d, const double2* Hinv, const double2* G1,
+                      const double2* G2, double2* D64, float2* D32, double2* xz, cudaStream_t s);
+void launch_rank_update(int math, int storage, int V, int nb, const void* Y, int k, const double2* D64,
+                        const float2* D32, double sign, const void* base, const NoiseSpec& ns, void* out,
+                        cudaStream_t s);
+void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s);
 
 // Deflation dots of Sec. 4.1 for a noise block:
 //   G1[i][col] = z_i^H b_col,  G2[i][col] = z_i^H gamma5 b_col

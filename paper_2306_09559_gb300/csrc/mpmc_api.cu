@@ -70,7 +70,15 @@ struct mpmc_ctx {
     double2* G2 = nullptr;
     double2* dterm = nullptr;
     double2* D = nullptr;         // projection coefficients k x nb
+    float2* D32 = nullptr;        // the same in FP32
     double2* xz = nullptr;        // b^H Z D per column
+    // projected composite (Sec. 4.3): Z and A Z in block layout, H^{-1}, 1/d_i
+    void* Zb = nullptr;
+    void* Wb = nullptr;
+    double2* d_invd = nullptr;
+    double2* gram_part = nullptr;
+    size_t gram_part_cap = 0;
+    bool proj_ready = false;
     int defl_nb = 0;
     // tensor-core deflation dots (reduced-precision handles)
     void* planes = nullptr;       // BF16 hi / lo planes of the deflation vectors, [2][Mpad][Kpad]
@@ -573,6 +581,8 @@ int ensure_defl_work(mpmc_ctx* h, int nb) {
     if (int rc = dev_alloc(h, &h->G2, sizeof(double2) * (size_t)h->k * nb)) return rc;
     if (int rc = dev_alloc(h, &h->dterm, sizeof(double2) * nb)) return rc;
     if (int rc = dev_alloc(h, &h->D, sizeof(double2) * (size_t)h->k * nb)) return rc;
+    dev_free(h->D32);
+    if (int rc = dev_alloc(h, &h->D32, sizeof(float2) * (size_t)h->k * nb)) return rc;
     if (int rc = dev_alloc(h, &h->xz, sizeof(double2) * nb)) return rc;
     h->defl_nb = nb;
     return MPMC_OK;
@@ -604,6 +614,13 @@ void free_deflation(mpmc_ctx* h) {
     dev_free(h->xz);
     dev_free(h->planes);
     dev_free(h->tc_part);
+    dev_free(h->D32);
+    dev_free(h->Zb);
+    dev_free(h->Wb);
+    dev_free(h->d_invd);
+    dev_free(h->gram_part);
+    h->gram_part_cap = 0;
+    h->proj_ready = false;
     h->tc_part_cap = 0;
     h->tc_ready = false;
     h->defl_nb = 0;
@@ -630,6 +647,139 @@ int upload_coefficients(mpmc_ctx* h) {
     return MPMC_OK;
 }
 
+
+// ------------------------------------------------------------------ projected composite (Sec. 4.3)
+// In-place inverse of a k x k complex matrix (Gauss-Jordan, partial pivoting).
+bool invert(std::vector<cd>& a, int k) {
+    std::vector<cd> inv((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) inv[(size_t)i * k + i] = 1.0;
+    for (int c = 0; c < k; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < k; ++r)
+            if (std::abs(a[(size_t)r * k + c]) > std::abs(a[(size_t)piv * k + c])) piv = r;
+        if (!(std::abs(a[(size_t)piv * k + c]) > 0)) return false;
+        if (piv != c)
+            for (int j = 0; j < k; ++j) {
+                std::swap(a[(size_t)piv * k + j], a[(size_t)c * k + j]);
+                std::swap(inv[(size_t)piv * k + j], inv[(size_t)c * k + j]);
+            }
+        const cd d = 1.0 / a[(size_t)c * k + c];
+        for (int j = 0; j < k; ++j) {
+            a[(size_t)c * k + j] *= d;
+            inv[(size_t)c * k + j] *= d;
+        }
+        for (int r = 0; r < k; ++r) {
+            if (r == c) continue;
+            const cd f = a[(size_t)r * k + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < k; ++j) {
+                a[(size_t)r * k + j] -= f * a[(size_t)c * k + j];
+                inv[(size_t)r * k + j] -= f * inv[(size_t)c * k + j];
+            }
+        }
+    }
+    a.swap(inv);
+    return true;
+}
+
+int proj_math(const mpmc_ctx* h) { return h->storage == ST_F64 ? ST_F64 : ST_F32; }
+
+int ensure_gram_part(mpmc_ctx* h, size_t entries) {
+    if (h->gram_part_cap >= entries) return MPMC_OK;
+    dev_free(h->gram_part);
+    h->gram_part_cap = 0;
+    if (int rc = dev_alloc(h, &h->gram_part, sizeof(double2) * entries)) return rc;
+    h->gram_part_cap = entries;
+    return MPMC_OK;
+}
+
+// Z and W = A Z in block layout, H = U^H W inverted, 1/d_i: everything the
+// projection needs, formed once per deflation set and gauge field.
+int ensure_projection(mpmc_ctx* h) {
+    if (h->proj_ready) return MPMC_OK;
+    if (h->k == 0) return fail(h, MPMC_ESTATE, "the projected composite needs deflation vectors");
+    const int k = h->k, math = proj_math(h);
+    const size_t bytes = (size_t)nsites12(h) * k * (math == ST_F64 ? 16 : 8);
+    dev_free(h->Zb);
+    dev_free(h->Wb);
+    dev_free(h->d_invd);
+    dev_free(h->d_Hinv);
+    if (int rc = dev_alloc(h, &h->Zb, bytes)) return rc;
+    if (int rc = dev_alloc(h, &h->Wb, bytes)) return rc;
+    launch_vec_to_block(math, h->g.V, k, h->Z, h->Zb, h->stream);
+    LAUNCHED(1);
+    StepArgs a{};
+    a.in = h->Zb;
+    a.out = h->Wb;
+    a.op_only = true;
+    a.kappa = h->kappa;
+    const NoiseSpec ns0{0, 0, 0};
+    launch_step(math, h->g, links_for(h, math), k, ns0, a, chain_config(h->g, k, 64, 1, 1), h->stream);
+    LAUNCHED(1);
+    const int nsplit = gram_nsplit(h->g.V);
+    if (int rc = ensure_gram_part(h, (size_t)nsplit * k * k + (size_t)k * k)) return rc;
+    double2* G = h->gram_part + (size_t)nsplit * k * k;
+    launch_block_gram(math, h->g.V, h->Zb, k, math, h->Wb, k, 1, h->gram_part, nsplit, G, h->stream);
+    LAUNCHED(2);
+    std::vector<double2> g((size_t)k * k);
+    CK(cudaMemcpyAsync(g.data(), G, sizeof(double2) * g.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // H_ij = u_i^H W_j = (z_pair(i)^H gamma5 W_j) / d_i
+    std::vector<cd> H((size_t)k * k);
+    std::vector<double2> invd(k);
+    for (int i = 0; i < k; ++i) {
+        const cd di = 1.0 / h->dnorm[i];
+        invd[i] = make_double2(di.real(), di.imag());
+        for (int j = 0; j < k; ++j) {
+            const double2 v = g[(size_t)h->pair[i] * k + j];
+            H[(size_t)i * k + j] = cd(v.x, v.y) * di;
+        }
+    }
+    if (!invert(H, k)) return fail(h, MPMC_ENONFINITE, "U^H A Z is singular");
+    std::vector<double2> hinv((size_t)k * k);
+    for (size_t q = 0; q < hinv.size(); ++q) {
+        if (!finite(H[q])) return fail(h, MPMC_ENONFINITE, "(U^H A Z)^{-1} is not finite");
+        hinv[q] = make_double2(H[q].real(), H[q].imag());
+    }
+    if (int rc = dev_alloc(h, &h->d_Hinv, sizeof(double2) * hinv.size())) return rc;
+    if (int rc = dev_alloc(h, &h->d_invd, sizeof(double2) * k)) return rc;
+    CK(cudaMemcpyAsync(h->d_Hinv, hinv.data(), sizeof(double2) * hinv.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_invd, invd.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->proj_ready = true;
+    return MPMC_OK;
+}
+
+// G1 = Z^H b, G2 = Z^H gamma5 b for the noise block (tensor or CUDA cores).
+int deflation_dots(mpmc_ctx* h, int nb, const NoiseSpec& ns) {
+    const bool tcore = h->storage != ST_F64 && h->use_tc && h->tc_ready;
+    if (int rc = prof_begin(h, PROF_DEFLATION, (double)h->k * nsites12(h) * (h->storage == ST_F64 ? 16 : 8)))
+        return rc;
+    if (tcore) {
+        int tsplit, kbps;
+        size_t pf;
+        tc_defl_plan(h->g.V, h->k, nb, &tsplit, &kbps, &pf);
+        if (h->tc_part_cap < pf) {
+            dev_free(h->tc_part);
+            h->tc_part_cap = 0;
+            if (int rc = dev_alloc(h, &h->tc_part, pf * sizeof(float))) return rc;
+            h->tc_part_cap = pf;
+        }
+        if (tc_defl_launch(h->tmap, h->g.V, h->k, nb, ns, h->tc_part, tsplit, kbps, h->G1, h->G2, h->d_err,
+                           h->stream))
+            return fail(h, MPMC_ECUDA, "tensor-core deflation kernel setup failed");
+        if (int rc = prof_end(h)) return rc;
+        LAUNCHED(2);
+    } else {
+        const int nsplit = defl_nsplit(h->g.V);
+        launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part, nsplit,
+                         h->stream);
+        if (int rc = prof_end(h)) return rc;
+        launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef, h->d_pair, h->G1, h->G2, h->dterm, h->stream);
+        LAUNCHED(3);
+    }
+    return MPMC_OK;
+}
 }  // namespace
 
 // ==================================================================== C ABI
@@ -748,6 +898,8 @@ int mpmc_set_poly(mpmc_handle h, int index, int kind, const double* roots, int n
         return fail(h, MPMC_EINVAL, "composite polynomial needs outer roots");
     if (kind == MPMC_DEFLATED_COMPOSITE && h->k == 0)
         return fail(h, MPMC_ESTATE, "projected composite needs mpmc_set_deflation first");
+    if (kind == MPMC_DEFLATED_COMPOSITE && index != 0)
+        return fail(h, MPMC_EINVAL, "the projected composite can only be polynomial 0 (the highest level)");
     if (kind == MPMC_DEFLATED_COMPOSITE && nouter < 2)
         return fail(h, MPMC_EINVAL, "projected composite needs at least two outer roots");
     PolyDef p;
@@ -897,10 +1049,13 @@ int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nr
     if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
     const PolyDef& p = h->polys[index];
     if (!p.set) return fail(h, MPMC_ESTATE, "polynomial not set");
-    if (p.kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "projected composite apply not built yet");
     const size_t n = nsites12(h);
     const int nb = std::min(default_nb(h), nrhs);
     if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    if (p.kind == MPMC_DEFLATED_COMPOSITE) {
+        if (int rc = ensure_defl_work(h, nb)) return rc;
+        if (int rc = ensure_projection(h)) return rc;
+    }
     const double* src = B;
     double* dst = X;
     if (!on_device) {
@@ -913,7 +1068,25 @@ int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nr
         const int cnt = std::min(nb, nrhs - c0);
         launch_import(h->storage, h->g.V, src, nrhs, c0, cnt, h->ws.r, nb, h->stream);
         LAUNCHED(1);
+        const bool proj = p.kind == MPMC_DEFLATED_COMPOSITE;
+        if (proj) {
+            // x = Z D + p_1(A) (B - (A Z) D),  D = H^{-1} U^H B,  U^H B from Z^H gamma5 B
+            const int nsplit = gram_nsplit(h->g.V);
+            if (int rc = ensure_gram_part(h, (size_t)nsplit * h->k * nb)) return rc;
+            launch_block_gram(proj_math(h), h->g.V, h->Zb, h->k, h->storage, h->ws.r, nb, 1, h->gram_part, nsplit,
+                              h->G2, h->stream);
+            launch_proj_coef(h->k, nb, h->d_pair, h->d_invd, h->d_Hinv, nullptr, h->G2, h->D, h->D32, nullptr,
+                             h->stream);
+            launch_rank_update(proj_math(h), h->storage, h->g.V, nb, h->Wb, h->k, h->D, h->D32, -1.0, h->ws.r,
+                               NoiseSpec{0, 0, 0}, h->ws.r, h->stream);
+            LAUNCHED(4);
+        }
         if (int rc = chain_apply(h, h->ws, p, h->ws.r, h->ws.x)) return rc;
+        if (proj) {
+            launch_rank_update(proj_math(h), h->storage, h->g.V, nb, h->Zb, h->k, h->D, h->D32, 1.0, h->ws.x,
+                               NoiseSpec{0, 0, 0}, h->ws.x, h->stream);
+            LAUNCHED(1);
+        }
         launch_export(h->storage, h->g.V, h->ws.x, nb, dst, nrhs, c0, cnt, h->stream);
         LAUNCHED(1);
     }
@@ -945,9 +1118,6 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
     if (nsamples < 1 || first < 0) return fail(h, MPMC_EINVAL, "nsamples must be >= 1 and first >= 0");
     const int L = num_levels(h);
     if (L == 0) return fail(h, MPMC_ESTATE, "no polynomial set");
-    for (int l = 0; l < L; ++l)
-        if (h->polys[l].kind == MPMC_DEFLATED_COMPOSITE)
-            return fail(h, MPMC_ENOTSUP, "projected composite trace not built yet");
     const int nb = std::min(default_nb(h), nsamples);
     if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
     if (int rc = ensure_defl_work(h, nb)) return rc;
@@ -959,53 +1129,42 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
         h->samples_cap = need;
     }
     Workspace& ws = h->ws;
-    const int nsplit = defl_nsplit(h->g.V);
+    if (h->polys[0].kind == MPMC_DEFLATED_COMPOSITE)
+        if (int rc = ensure_projection(h)) return rc;
     for (int l = 0; l < L; ++l) {
         const bool has_lo = l + 1 < L;
+        const bool proj = h->polys[l].kind == MPMC_DEFLATED_COMPOSITE;
         const bool defl = has_lo && h->k > 0;
         for (int b0 = 0; b0 < nsamples; b0 += nb) {
             const int nvalid = std::min(nb, nsamples - b0);
             const NoiseSpec ns{seed, (uint32_t)l, (uint32_t)(first + b0)};
             cd c_hi = 0.0, c_lo = 0.0;
-            if (int rc = chain_trace(h, ws, h->polys[l], ns, nullptr, ws.acc_hi, &c_hi)) return rc;
+            if (defl || proj)
+                if (int rc = deflation_dots(h, nb, ns)) return rc;
+            if (proj) {
+                // r = b - (A Z) D with D = H^{-1} U^H b; the sample adds b^H Z D
+                launch_proj_coef(h->k, nb, h->d_pair, h->d_invd, h->d_Hinv, h->G1, h->G2, h->D, h->D32, h->xz,
+                                 h->stream);
+                launch_rank_update(proj_math(h), h->storage, h->g.V, nb, h->Wb, h->k, h->D, h->D32, -1.0, nullptr,
+                                   ns, ws.r, h->stream);
+                LAUNCHED(2);
+                if (int rc = chain_trace(h, ws, h->polys[l], ns, ws.r, ws.acc_hi, &c_hi)) return rc;
+            } else {
+                if (int rc = chain_trace(h, ws, h->polys[l], ns, nullptr, ws.acc_hi, &c_hi)) return rc;
+            }
             if (has_lo)
                 if (int rc = chain_trace(h, ws, h->polys[l + 1], ns, nullptr, ws.acc_lo, &c_lo)) return rc;
             if (defl) {
-                const bool tcore = h->storage != ST_F64 && h->use_tc && h->tc_ready;
-                const double zbytes = (double)h->k * nsites12(h) * (h->storage == ST_F64 ? 16 : (tcore ? 8 : 8));
-                if (int rc = prof_begin(h, PROF_DEFLATION, zbytes)) return rc;
-                if (tcore) {
-                    int tsplit, kbps;
-                    size_t pf;
-                    tc_defl_plan(h->g.V, h->k, nb, &tsplit, &kbps, &pf);
-                    if (h->tc_part_cap < pf) {
-                        dev_free(h->tc_part);
-                        h->tc_part_cap = 0;
-                        if (int rc = dev_alloc(h, &h->tc_part, pf * sizeof(float))) return rc;
-                        h->tc_part_cap = pf;
-                    }
-                    if (tc_defl_launch(h->tmap, h->g.V, h->k, nb, ns, h->tc_part, tsplit, kbps, h->G1, h->G2,
-                                       h->d_err, h->stream))
-                        return fail(h, MPMC_ECUDA, "tensor-core deflation kernel setup failed");
-                    if (int rc = prof_end(h)) return rc;
-                    launch_defl_term(h->k, nb, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1, h->G2, h->dterm,
-                                     h->stream);
-                    LAUNCHED(3);
-                } else {
-                    launch_defl_dots(h->storage == ST_F64 ? ST_F64 : ST_F32, h->g, h->k, h->Z, nb, ns, h->defl_part,
-                                     nsplit, h->stream);
-                    if (int rc = prof_end(h)) return rc;
-                    launch_defl_reduce(h->k, nb, nsplit, h->defl_part, h->d_coef + (size_t)l * h->k, h->d_pair,
-                                       h->G1, h->G2, h->dterm, h->stream);
-                    LAUNCHED(3);
-                }
+                launch_defl_term(h->k, nb, h->d_coef + (size_t)l * h->k, h->d_pair, h->G1, h->G2, h->dterm,
+                                 h->stream);
+                LAUNCHED(1);
             }
             double chi[2], clo[2];
             setc(chi, c_hi);
             setc(clo, c_lo);
             launch_finalize(ws.acc_rows, nb, nvalid, ws.acc_hi, has_lo ? ws.acc_lo : nullptr, chi, clo,
                             defl ? h->dterm : nullptr, h->samples + (size_t)l * nsamples + b0, nullptr, nullptr,
-                            h->stream);
+                            h->stream, proj ? h->xz : nullptr);
             LAUNCHED(1);
         }
     }
@@ -1179,6 +1338,7 @@ int mpmc_set_links(mpmc_handle h, const double* links) {
     CK(cudaMemcpyAsync(h->io, links, nl * 16, cudaMemcpyHostToDevice, h->stream));
     launch_links(ST_F64, h->g.V, h->io, h->links64, h->stream);
     LAUNCHED(1);
+    h->proj_ready = false;   // A Z changes with the links
     if (h->links32) {
         launch_links(ST_F32, h->g.V, h->io, h->links32, h->stream);
         LAUNCHED(1);

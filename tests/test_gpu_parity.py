@@ -242,6 +242,79 @@ def test_trace_block_size_does_not_change_samples():
         assert np.max(np.abs(o - out[0])) < 1e-12 * op.n
 
 
+# ---------------------------------------------------------------- projected composite (Sec. 4.3)
+def _projected(polys):
+    return [dict(polys[0], kind="deflated_composite")] + list(polys[1:])
+
+
+def test_apply_projected_composite_fp64():
+    op, polys, lam, Z, pair = small_setup()
+    defl = M.Deflation(op, Z, lam, pair)
+    pp = _projected(polys)
+    B = synth.random_block(op.n, 11, 13)
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_block(8)
+        h.mpmc_set_deflation(Z, lam, pair)
+        set_polys(h, pp)
+        X = h.mpmc_apply_poly(0, B)
+    ref = M.apply_spec(op, pp[0], B, defl)
+    assert np.linalg.norm(X - ref) <= 1e-11 * np.linalg.norm(ref)
+    # it maps A z_i to z_i (the projection is exact on the deflation space)
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        set_polys(h, pp)
+        AZ = h.mpmc_apply_op(Z)
+        back = h.mpmc_apply_poly(0, AZ)
+    assert np.linalg.norm(back - Z) < 1e-9 * np.linalg.norm(Z)
+
+
+@pytest.mark.parametrize("nsamples,block", [(21, 8), (9, 32)])
+def test_trace_projected_composite_fp64_per_sample(nsamples, block):
+    op, polys, lam, Z, pair = small_setup()
+    defl = M.Deflation(op, Z, lam, pair)
+    pp = _projected(polys)
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_block(block)
+        h.mpmc_set_deflation(Z, lam, pair)
+        set_polys(h, pp)
+        mean, var, s = h.mpmc_trace_levels(seed=808, nsamples=nsamples, first=2)
+        corr = h.mpmc_level_info(0)[0]
+    ref, hi, lo, dt = M.level_sample_parts(op, pp, 0, 808, nsamples, defl, first=2)
+    scale = np.abs(hi) + np.abs(lo) + np.abs(dt)
+    assert np.max(np.abs(s[0] - ref) / scale) < 1e-12
+    assert abs(corr - M.exact_correction(pp, 0, defl)) < 1e-10 * (1 + abs(corr))
+    # the other levels are unchanged
+    for level in (1, 2):
+        r2, hi2, lo2, dt2 = M.level_sample_parts(op, pp, level, 808, nsamples, defl, first=2)
+        assert np.max(np.abs(s[level] - r2) / (np.abs(hi2) + np.abs(lo2) + np.abs(dt2))) < 1e-12
+
+
+def test_trace_projected_composite_fp32_paired():
+    op, polys, lam, Z, pair = small_setup()
+    defl = M.Deflation(op, Z, lam, pair)
+    pp = _projected(polys)
+    N = 40
+    with handle((4, 4, 4, 4), prec=G.FP32) as h:
+        h.mpmc_set_block(20)
+        h.mpmc_set_deflation(Z, lam, pair)
+        set_polys(h, pp)
+        _, _, s = h.mpmc_trace_levels(seed=9, nsamples=N)
+    ref, hi, lo, dt = M.level_sample_parts(op, pp, 0, 9, N, defl)
+    d = s[0] - ref
+    floor = 1e-7 * np.mean(np.abs(hi) + np.abs(lo))
+    assert abs(np.mean(d.real)) <= 0.1 * np.std(ref.real, ddof=1) / np.sqrt(N) + floor
+    assert np.std(d.real) <= 0.3 * np.std(ref.real) + floor
+
+
+def test_projected_composite_only_at_the_top():
+    with handle((2, 2, 2, 2)) as h:
+        Z = synth.random_block(h.n, 2, 3)
+        h.mpmc_set_deflation(Z, [1.0 + 0.1j, 1.0 - 0.1j], [1, 0])
+        with pytest.raises(G.MpmcError) as e:
+            h.mpmc_set_poly(1, G.DEFLATED_COMPOSITE, [1.0], [1.0, 2.0])
+        assert e.value.code == G.MPMC_EINVAL
+
+
 # ---------------------------------------------------------------- deflation dots
 def _zhat(Z):
     """z rounded as the reduced-precision handles store it: hi = bf16(z), lo = bf16(z - hi)."""
