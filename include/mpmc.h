@@ -298,6 +298,30 @@ MPMC_API int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int fi
                                  double* G2);
 
 /*
+ * mpmc_set_deflation_device: as mpmc_set_deflation, with Z a device
+ * pointer (same layout); lambda and pair stay on the host.
+ */
+MPMC_API int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k);
+
+/*
+ * mpmc_vector_stats: for k device vectors z_i (vector-major, complex double,
+ * vector i at Z + 2*n*i) writes stats[4i..4i+3] = (|z_i|^2, |A z_i|^2,
+ * Re z_i^H A z_i, Im z_i^H A z_i), with A applied in FP64.  These give the
+ * Rayleigh quotient lambda_i = z_i^H A z_i / |z_i|^2 and every residual norm
+ * |A z_i - mu z_i| the eigen selection of Sec. 4 needs in closed form.
+ */
+MPMC_API int mpmc_vector_stats(mpmc_handle h, const double* Z, int k, double* stats);
+
+/*
+ * mpmc_project: the Left-right Projection of Sec. 2.1 with the deflation
+ * vectors (V = Z, U = the gamma5 left vectors): R = B - A Z H^{-1} U^H B,
+ * H = U^H A Z, for nrhs vectors in the block layout (host or device per
+ * on_device).  Sec. 5, step 2c starts the PP-GMRES of the deflated
+ * polynomial from such a projected Z4 vector.
+ */
+MPMC_API int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, int on_device);
+
+/*
  * mpmc_trace_poly_noalloc: Hutchinson samples s_j = b_j^H p(A) b_j of one
  * polynomial, j = first .. first+nsamples-1 (Z4 noise of level id `level`,
  * same bits as mpmc_noise), computed without allocating any device memory.

@@ -110,6 +110,9 @@ void launch_rank_update(int math, int storage, int V, int nb, const void* Y, int
                         const float2* D32, double sign, const void* base, const NoiseSpec& ns, void* out,
                         cudaStream_t s);
 void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s);
+// out[c] = (|x_c|^2, |y_c|^2, Re x_c^H y_c, Im x_c^H y_c) for FP64 blocks of nb columns
+void launch_col_stats(int V, int nb, const double* X, const double* Y, double* part, int nsplit, double* out,
+                      cudaStream_t s);
 
 // Deflation dots of Sec. 4.1 for a noise block:
 //   G1[i][col] = z_i^H b_col,  G2[i][col] = z_i^H gamma5 b_col

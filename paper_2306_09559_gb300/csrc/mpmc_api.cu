@@ -940,7 +940,8 @@ int mpmc_get_roots(mpmc_handle h, int index, double* roots, double* outer) {
     return MPMC_OK;
 }
 
-int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+static int set_deflation_impl(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k,
+                              int on_device) {
     if (!h) return MPMC_EINVAL;
     const long long n = nsites12(h);
     if (k < 0 || k > n || k > 4096) return fail(h, MPMC_EINVAL, "k out of range");
@@ -964,7 +965,8 @@ int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, con
     const size_t ncplx = (size_t)n * k;
     const int zst = h->storage == ST_F64 ? ST_F64 : ST_F32;
     if (int rc = ensure_io(h, ncplx)) return rc;
-    CK(cudaMemcpyAsync(h->io, Z, ncplx * 16, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->io, Z, ncplx * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
     if (int rc = dev_alloc(h, &h->Z, ncplx * (zst == ST_F64 ? 16 : 8))) return rc;
     if (zst == ST_F64) {
         launch_convert_vectors(zst, ncplx, h->io, h->Z, h->stream);
@@ -1490,6 +1492,84 @@ int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int first, int 
         CK(cudaMemset(h->d_err, 0, sizeof(int)));
         return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (tensor-core deflation pipeline)");
     }
+    return MPMC_OK;
+}
+
+int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+    return set_deflation_impl(h, Z, lambda, pair, k, 0);
+}
+
+int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+    return set_deflation_impl(h, Z, lambda, pair, k, 1);
+}
+
+int mpmc_vector_stats(mpmc_handle h, const double* Z, int k, double* stats) {
+    if (!h) return MPMC_EINVAL;
+    if (!Z || !stats || k < 1) return fail(h, MPMC_EINVAL, "bad vector_stats arguments");
+    const int chunk = std::min(k, 64);
+    if (int rc = ensure_ws(h, h->ws64, ST_F64, chunk)) return rc;
+    const int nsplit = gram_nsplit(h->g.V);
+    if (int rc = ensure_gram_part(h, (size_t)(nsplit + 1) * chunk * 2)) return rc;
+    double* part = reinterpret_cast<double*>(h->gram_part);
+    double* out = part + (size_t)nsplit * chunk * 4;
+    Workspace& ws = h->ws64;
+    std::vector<double> host((size_t)chunk * 4);
+    for (int c0 = 0; c0 < k; c0 += chunk) {
+        const int cnt = std::min(chunk, k - c0);
+        // columns c0..c0+cnt of the vector-major input -> block layout (zero padded)
+        CK(cudaMemsetAsync(ws.w[0], 0, (size_t)nsites12(h) * chunk * 16, h->stream));
+        launch_vec_to_block(ST_F64, h->g.V, cnt, Z + (size_t)c0 * nsites12(h) * 2, ws.w[0], h->stream);
+        if (cnt != chunk) {
+            // vec_to_block wrote a block of width cnt: re-layout into width `chunk` through w[2]
+            launch_import(ST_F64, h->g.V, reinterpret_cast<const double*>(ws.w[0]), cnt, 0, cnt, ws.w[2], chunk,
+                          h->stream);
+            CK(cudaMemcpyAsync(ws.w[0], ws.w[2], (size_t)nsites12(h) * chunk * 16, cudaMemcpyDeviceToDevice,
+                               h->stream));
+        }
+        LAUNCHED(cnt != chunk ? 2 : 1);
+        if (int rc = apply_A(h, ws, ws.w[0], ws.w[1])) return rc;
+        launch_col_stats(h->g.V, chunk, reinterpret_cast<const double*>(ws.w[0]),
+                         reinterpret_cast<const double*>(ws.w[1]), part, nsplit, out, h->stream);
+        LAUNCHED(2);
+        CK(cudaMemcpyAsync(host.data(), out, sizeof(double) * 4 * chunk, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        std::copy(host.begin(), host.begin() + 4 * cnt, stats + 4 * (size_t)c0);
+    }
+    return MPMC_OK;
+}
+
+int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, int on_device) {
+    if (!h) return MPMC_EINVAL;
+    if (!B || !R || nrhs < 1) return fail(h, MPMC_EINVAL, "bad project arguments");
+    if (h->k == 0) return fail(h, MPMC_ESTATE, "no deflation vectors set");
+    const size_t n = nsites12(h);
+    const int nb = std::min(default_nb(h), nrhs);
+    if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    if (int rc = ensure_defl_work(h, nb)) return rc;
+    if (int rc = ensure_projection(h)) return rc;
+    const double* src = B;
+    double* dst = R;
+    if (!on_device) {
+        if (int rc = ensure_io(h, n * nrhs)) return rc;
+        CK(cudaMemcpyAsync(h->io, B, n * nrhs * 16, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+        dst = h->io;
+    }
+    const int nsplit = gram_nsplit(h->g.V);
+    if (int rc = ensure_gram_part(h, (size_t)nsplit * h->k * nb)) return rc;
+    for (int c0 = 0; c0 < nrhs; c0 += nb) {
+        const int cnt = std::min(nb, nrhs - c0);
+        launch_import(h->storage, h->g.V, src, nrhs, c0, cnt, h->ws.r, nb, h->stream);
+        launch_block_gram(proj_math(h), h->g.V, h->Zb, h->k, h->storage, h->ws.r, nb, 1, h->gram_part, nsplit, h->G2,
+                          h->stream);
+        launch_proj_coef(h->k, nb, h->d_pair, h->d_invd, h->d_Hinv, nullptr, h->G2, h->D, h->D32, nullptr, h->stream);
+        launch_rank_update(proj_math(h), h->storage, h->g.V, nb, h->Wb, h->k, h->D, h->D32, -1.0, h->ws.r,
+                           NoiseSpec{0, 0, 0}, h->ws.r, h->stream);
+        launch_export(h->storage, h->g.V, h->ws.r, nb, dst, nrhs, c0, cnt, h->stream);
+        LAUNCHED(6);
+    }
+    if (!on_device) CK(cudaMemcpyAsync(R, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return MPMC_OK;
 }
 

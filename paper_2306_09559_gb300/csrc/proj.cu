@@ -131,6 +131,37 @@ __global__ void k_vec_to_block(int V, int k, const T* __restrict__ src, T* dst) 
     dst[idx * 2 + 1] = src[((size_t)i * V * 12 + row) * 2 + 1];
 }
 
+// Per column c of two blocks X, Y ([site][e][nb], FP64): partial sums of |x|^2, |y|^2, x^H y.
+__global__ void k_col_stats(int V, int nb, const double* __restrict__ X, const double* __restrict__ Y, double* part,
+                            int nsplit) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int split = blockIdx.y;
+    if (c >= nb) return;
+    const int chunk = (V + nsplit - 1) / nsplit;
+    const int s0 = split * chunk, s1 = min(V, s0 + chunk);
+    double xx = 0, yy = 0, re = 0, im = 0;
+    for (int site = s0; site < s1; ++site)
+        for (int e = 0; e < 12; ++e) {
+            const size_t o = (((size_t)site * 12 + e) * nb + c) * 2;
+            const double xr = X[o], xi = X[o + 1], yr = Y[o], yi = Y[o + 1];
+            xx += xr * xr + xi * xi;
+            yy += yr * yr + yi * yi;
+            re += xr * yr + xi * yi;
+            im += xr * yi - xi * yr;
+        }
+    double* q = part + ((size_t)split * nb + c) * 4;
+    q[0] = xx; q[1] = yy; q[2] = re; q[3] = im;
+}
+
+__global__ void k_col_stats_reduce(int nb, int nsplit, const double* __restrict__ part, double* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    double a[4] = {0, 0, 0, 0};
+    for (int s = 0; s < nsplit; ++s)
+        for (int t = 0; t < 4; ++t) a[t] += part[((size_t)s * nb + c) * 4 + t];
+    for (int t = 0; t < 4; ++t) out[(size_t)c * 4 + t] = a[t];
+}
+
 NoiseKey key_of(const NoiseSpec& ns) {
     NoiseKey nk;
     nk.k0 = (uint32_t)(ns.seed & 0xffffffffu);
@@ -185,6 +216,12 @@ void launch_rank_update(int math, int storage, int V, int nb, const void* Y, int
                                                                       (const __nv_bfloat16*)base, nk,
                                                                       (__nv_bfloat16*)out);
     }
+}
+
+void launch_col_stats(int V, int nb, const double* X, const double* Y, double* part, int nsplit, double* out,
+                      cudaStream_t s) {
+    k_col_stats<<<dim3(nblk(nb, 64), nsplit), 64, 0, s>>>(V, nb, X, Y, part, nsplit);
+    k_col_stats_reduce<<<nblk(nb, 64), 64, 0, s>>>(nb, nsplit, part, out);
 }
 
 void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s) {

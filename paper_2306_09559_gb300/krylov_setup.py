@@ -79,7 +79,12 @@ class Setup:
         return harmonic_ritz(hbar, m_out), m_out
 
     def ritz_pairs(self, inner_roots, v0, m, nev):
-        """PP-Arnoldi Ritz vectors (n x nev, host) nearest the origin and lambda = z^H A z."""
+        """PP-Arnoldi Ritz vectors nearest the origin, kept on the device.
+
+        Returns (lam, Zd, stats): Zd is a CUDA tensor (nev, n) of unit Ritz
+        vectors of A p_in(A); stats[i] = (|z|^2, |Az|^2, Re z^H Az, Im z^H Az)
+        from the library (A in FP64); lam_i = z_i^H A z_i / |z_i|^2.
+        """
         import torch
         self.h.mpmc_set_poly(self.SLOT, G.SINGLE, inner_roots, leja=True)
         basis = torch.zeros((m + 1, self.h.n), dtype=torch.complex128, device="cuda")
@@ -90,48 +95,64 @@ class Setup:
         Zd = torch.zeros((idx.size, self.h.n), dtype=torch.complex128, device="cuda")
         self.h.mpmc_combine(basis, k, Y[:, idx], Zd)
         torch.cuda.synchronize()
-        Z = Zd.cpu().numpy().T.copy()
-        del basis, Zd
-        Z /= np.linalg.norm(Z, axis=0)
-        AZ = self.h.mpmc_apply_op(Z)
-        lam = np.einsum("ni,ni->i", Z.conj(), AZ)
-        return lam, Z, AZ
+        del basis
+        stats = self.h.mpmc_vector_stats(Zd)
+        lam = (stats[:, 2] + 1j * stats[:, 3]) / stats[:, 0]
+        return lam, Zd, stats
 
     @staticmethod
-    def select(lam, Z, AZ, imaglim=IMAGLIM, evectol=EVECTOL, kmax=None):
+    def select(lam, stats, imaglim=IMAGLIM, evectol=EVECTOL, kmax=None):
         """The acceptance rule of Sec. 4 on candidates sorted by |lambda|.
 
-        Left residual of u = gamma5 z_j for eigenvalue lambda_i: since
-        A^H = gamma5 A gamma5 and gamma5 is unitary,
-        ||A^H u - conj(lambda_i) u|| = ||A z_j - conj(lambda_i) z_j||.
+        Residual norms come from the per-vector statistics in closed form:
+        |A z - mu z|^2 = |Az|^2 - 2 Re(conj(mu) z^H A z) + |mu|^2 |z|^2.  The
+        left residual of u = gamma5 z_j for eigenvalue lambda_i is
+        |A^H u - conj(lambda_i) u| = |A z_j - conj(lambda_i) z_j| because
+        A^H = gamma5 A gamma5 and gamma5 is unitary.
+        Returns (indices into the candidates, pair map of the kept list).
         """
-        order = np.argsort(np.abs(lam), kind="stable")
-        lam, Z, AZ = lam[order], Z[:, order], AZ[:, order]
+        zz, aa, zaz = stats[:, 0], stats[:, 1], stats[:, 2] + 1j * stats[:, 3]
 
         def res(i, val):
-            return np.linalg.norm(AZ[:, i] - val * Z[:, i]) / np.linalg.norm(Z[:, i])
+            r2 = aa[i] - 2 * np.real(np.conj(val) * zaz[i]) + abs(val) ** 2 * zz[i]
+            return np.sqrt(max(r2, 0.0) / zz[i])
 
+        order = np.argsort(np.abs(lam), kind="stable")
         keep, pair = [], []
-        i = 0
-        while i < lam.size and (kmax is None or len(keep) < kmax):
+        p = 0
+        while p < order.size and (kmax is None or len(keep) < kmax):
+            i = order[p]
             if abs(lam[i].imag) < imaglim:
                 if res(i, lam[i]) < evectol and res(i, np.conj(lam[i])) < evectol:
                     pair.append(len(keep))
                     keep.append(i)
-                i += 1
-            elif i + 1 < lam.size and abs(lam[i + 1] - np.conj(lam[i])) < imaglim:
-                ok = (res(i, lam[i]) < evectol and res(i + 1, lam[i + 1]) < evectol
-                      and res(i + 1, np.conj(lam[i])) < evectol and res(i, np.conj(lam[i + 1])) < evectol)
+                p += 1
+            elif p + 1 < order.size and abs(lam[order[p + 1]] - np.conj(lam[i])) < imaglim:
+                j = order[p + 1]
+                ok = (res(i, lam[i]) < evectol and res(j, lam[j]) < evectol
+                      and res(j, np.conj(lam[i])) < evectol and res(i, np.conj(lam[j])) < evectol)
                 if ok and (kmax is None or len(keep) + 2 <= kmax):
                     a = len(keep)
-                    keep += [i, i + 1]
+                    keep += [i, j]
                     pair += [a + 1, a]
-                i += 2
+                p += 2
             else:
-                i += 1
-        keep = np.array(keep, dtype=np.int64)
-        return lam[keep], Z[:, keep], np.array(pair, dtype=np.int32)
+                p += 1
+        return np.array(keep, dtype=np.int64), np.array(pair, dtype=np.int32)
 
     def eigenpairs(self, inner_roots, v0, m, ndefinit, kmax=None, imaglim=IMAGLIM, evectol=EVECTOL):
-        lam, Z, AZ = self.ritz_pairs(inner_roots, v0, m, ndefinit)
-        return self.select(lam, Z, AZ, imaglim, evectol, kmax)
+        """(Zd, lam, pair): accepted eigenvectors as a CUDA tensor (k, n), eigenvalues, pairing."""
+        import torch
+        lam, Zd, stats = self.ritz_pairs(inner_roots, v0, m, ndefinit)
+        keep, pair = self.select(lam, stats, imaglim, evectol, kmax)
+        Zsel = Zd[torch.as_tensor(keep, device=Zd.device)].contiguous() if keep.size else Zd[:0]
+        return Zsel, lam[keep], pair
+
+    def projected_start(self, seed):
+        """A Z4 vector after one Left-right Projection, normalised (Sec. 5, step 2c).
+
+        Needs the deflation vectors set on the setup handle.
+        """
+        b = self.h.mpmc_noise(seed, 99, 0, 1)
+        r = self.h.mpmc_project(b)[:, 0]
+        return r / np.linalg.norm(r)

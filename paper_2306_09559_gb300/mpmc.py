@@ -65,6 +65,10 @@ _SIGS = {
     "mpmc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "mpmc_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "mpmc_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mpmc_set_deflation_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_int]),
+    "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "mpmc_deflation_dots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -291,6 +295,23 @@ class Handle:
         v = ctypes.c_int()
         self._check(self._L.mpmc_get_option(self._h, int(option), ctypes.byref(v)), "mpmc_get_option")
         return v.value
+
+    def mpmc_set_deflation_device(self, Zd, lam, pair):
+        """Zd: CUDA complex128 tensor (k, n), row i = z_i."""
+        lam = _c128(lam)
+        pr = np.ascontiguousarray(pair, dtype=np.int32)
+        self._check(self._L.mpmc_set_deflation_device(self._h, _ptr(Zd), _ptr(lam), _ptr(pr), int(Zd.shape[0])),
+                    "mpmc_set_deflation_device")
+
+    def mpmc_vector_stats(self, Zd):
+        """Zd: CUDA complex128 tensor (k, n); returns (k, 4) float64 stats."""
+        k = int(Zd.shape[0])
+        out = np.zeros((k, 4), dtype=np.float64)
+        self._check(self._L.mpmc_vector_stats(self._h, _ptr(Zd), k, _ptr(out)), "mpmc_vector_stats")
+        return out
+
+    def mpmc_project(self, B):
+        return self._block_call(self._L.mpmc_project, "mpmc_project", B)
 
     def mpmc_deflation_dots(self, seed, level, first, nrhs, k):
         G1 = np.zeros((k, nrhs), dtype=np.complex128)

@@ -47,10 +47,7 @@ class Workload:
         return 12 * self.V
 
     def degrees(self):
-        out = []
-        for lv in self.levels:
-            out.append(lv[1] if lv[0] == "single" else lv[1] * lv[2] - 1)
-        return out
+        return [lv[1] if lv[0] == "single" else lv[1] * lv[2] - 1 for lv in self.levels]
 
     def applies_per_step(self):
         """Noise-vector polynomial applications in one pass over all levels."""
@@ -69,7 +66,11 @@ class Workload:
         lat = f"{lx}x{ly}x{lz}x{lt}"
         lv = []
         for x in self.levels:
-            lv.append(f"deg{x[1]}" if x[0] == "single" else f"composite{x[2]}x{x[1]}=deg{x[1] * x[2] - 1}")
+            if x[0] == "single":
+                lv.append(f"deg{x[1]}")
+            else:
+                tag = "projected-composite" if x[0] == "deflated_composite" else "composite"
+                lv.append(f"{tag}{x[2]}x{x[1]}=deg{x[1] * x[2] - 1}")
         return (f"Wilson-Dirac {lat} {self.links} eps={self.eps} kappa={self.kappa}; levels "
                 f"[{', '.join(lv)}]; {self.k} deflation eigenpairs; {self.nsamples} Z4 noises/level")
 
@@ -82,9 +83,14 @@ WORKLOADS = {
     "8^4": Workload("8^4", (8, 8, 8, 8), "near_identity", 1, 0.3, 0.123,
                     (("composite", 10, 20), ("single", 50), ("single", 10)), 50, 512, 1002, 2002,
                     arnoldi_m=320, ndefinit=200, block=512),
+    # HBM-resident lattice: BF16-stored vectors, 200 eigenpairs, 256 noises/level
     "16^3x32": Workload("16^3x32", (16, 16, 16, 32), "near_identity", 2, 0.25, 0.1235,
                         (("composite", 20, 30), ("single", 100), ("single", 16)), 200, 256, 1003, 2003,
-                        arnoldi_m=400, ndefinit=260, block=32),
+                        arnoldi_m=640, ndefinit=420, block=32),
+    # near-critical 24^3 x 32: projected composite 50 x 20 (Sec. 4.3), 100 eigenpairs
+    "24^3x32": Workload("24^3x32", (24, 24, 24, 32), "near_identity", 3, 0.2, 0.1240,
+                        (("deflated_composite", 20, 50), ("single", 100), ("single", 16)), 100, 64, 1004, 2004,
+                        arnoldi_m=480, ndefinit=220, block=16),
 }
 
 
@@ -99,41 +105,58 @@ def gauge(wl):
 
 
 def setup(h64, wl, log=None):
-    """Polynomials [(kind, roots, outer)] and deflation (Z n x k, lam, pair) for a workload."""
+    """Polynomials [(kind, roots, outer)] and deflation (Zd (k, n) CUDA tensor, lam, pair).
+
+    Order of Sec. 5, step 2: one GMRES run for the single polynomials and
+    p_in (2a); PP-Arnoldi eigenpairs with p_in and the Sec. 4 selection (2b);
+    p_out from GMRES on A p_in(A), started from the random vector for a plain
+    composite, or from a Z4 vector after one Left-right Projection for the
+    projected composite (2c).
+    """
     S = krylov_setup.Setup(h64)
     v0 = synth.random_unit_vector(wl.n, wl.setup_seed)
     singles = [lv[1] for lv in wl.levels if lv[0] == "single"]
-    inners = [lv[1] - 1 for lv in wl.levels if lv[0] == "composite"]
+    inners = [lv[1] - 1 for lv in wl.levels if lv[0] != "single"]
     degs = sorted(set(singles + inners))
     roots = dict(zip(degs, S.single_roots(v0, degs)))
-    polys = []
-    inner = None
-    for lv in wl.levels:
-        if lv[0] == "single":
-            polys.append(("single", roots[lv[1]], None))
-        else:
-            inner = roots[lv[1] - 1]
-            outer, _ = S.pp_roots(inner, v0, m_out=lv[2])
-            polys.append(("composite", inner, outer))
+    pin = roots[inners[0]] if inners else roots[min(degs)]
     defl = None
     if wl.k > 0:
-        pin = inner if inner is not None else roots[min(degs)]
-        lam, Z, pair = S.eigenpairs(pin, v0, wl.arnoldi_m, wl.ndefinit, kmax=wl.k)
+        Zd, lam, pair = S.eigenpairs(pin, v0, wl.arnoldi_m, wl.ndefinit, kmax=wl.k)
         if log:
             log(f"setup: {lam.size} of {wl.ndefinit} Ritz pairs accepted (want {wl.k}); "
                 f"|lambda| in [{np.abs(lam).min():.4g}, {np.abs(lam).max():.4g}]")
-        defl = (Z, lam, pair)
+        defl = (Zd, lam, pair)
+        h64.mpmc_set_deflation_device(Zd, lam, pair)
+    polys = []
+    for lv in wl.levels:
+        if lv[0] == "single":
+            polys.append(("single", roots[lv[1]], None))
+            continue
+        inner = roots[lv[1] - 1]
+        start = v0
+        if lv[0] == "deflated_composite":
+            if defl is None:
+                raise ValueError("a projected composite needs deflation eigenpairs")
+            start = S.projected_start(wl.setup_seed)
+        outer, _ = S.pp_roots(inner, start, m_out=lv[2])
+        polys.append((lv[0], inner, outer))
     return polys, defl
 
 
 def configure(h, polys, defl, block=None):
     """Load a workload's polynomials and deflation into a handle."""
     if defl is not None:
-        h.mpmc_set_deflation(*defl)
+        Z, lam, pair = defl
+        if hasattr(Z, "is_cuda") and Z.is_cuda:
+            h.mpmc_set_deflation_device(Z, lam, pair)
+        else:
+            h.mpmc_set_deflation(Z, lam, pair)
+    kinds = {"single": G.SINGLE, "composite": G.COMPOSITE, "deflated_composite": G.DEFLATED_COMPOSITE}
     for i, (kind, r, o) in enumerate(polys):
         if kind == "single":
             h.mpmc_set_poly(i, G.SINGLE, r, leja=True)
         else:
-            h.mpmc_set_poly(i, G.COMPOSITE, r, o, leja=True)
+            h.mpmc_set_poly(i, kinds[kind], r, o, leja=True)
     if block:
         h.mpmc_set_block(block)

@@ -416,6 +416,46 @@ def test_combine_forms_ritz_vectors():
     assert np.max(np.abs(Zg - V[:, :m] @ Y)) < 1e-12 * np.max(np.abs(Zg))
 
 
+# ---------------------------------------------------------------- product-side setup
+def test_product_setup_matches_oracle_setup():
+    """Roots and accepted eigenpairs of the GPU setup agree with the oracle's (Sec. 5, step 2)."""
+    from paper_2306_09559_gb300 import krylov_setup
+    dims, kappa = (4, 4, 4, 4), 0.12
+    op = operator(dims, "haar", 0, kappa)
+    v0 = synth.random_unit_vector(op.n, 17)
+    with handle(dims, kappa=kappa) as h:
+        S = krylov_setup.Setup(h)
+        r24, r4 = S.single_roots(v0, [24, 4])
+        Zd, lam, pair = S.eigenpairs(r4, v0, m=120, ndefinit=24)
+        out5, _ = S.pp_roots(r4, v0, m_out=6)
+    o24, o4 = K.gmres_polynomials(op, v0, [24, 4])
+    oout, _, _ = K.pp_gmres_roots(op, o4, v0, m_out=6)
+    for got, ref in ((r24, o24), (r4, o4), (out5, oout)):
+        d = np.abs(got[:, None] - ref[None, :])
+        assert np.max(np.min(d, axis=1)) < 1e-8 and np.max(np.min(d, axis=0)) < 1e-8
+    olam, oZ = K.pp_arnoldi_ritz(op, o4, v0, m=120, nev=24)
+    olam_s, _, opair = K.select_deflation(op, op.gamma5, olam, oZ)
+    assert lam.size == olam_s.size and lam.size > 0
+    d = np.abs(lam[:, None] - olam_s[None, :])
+    assert np.max(np.min(d, axis=1)) < 1e-8
+    assert np.array_equal(np.sort(pair - np.arange(pair.size)), np.sort(opair - np.arange(opair.size)))
+    # the accepted vectors are eigenvectors of A to the selection tolerance
+    Z = Zd.cpu().numpy().T
+    assert np.max(np.linalg.norm(op(Z) - Z * lam, axis=0)) < K.EVECTOL
+
+
+def test_left_right_projection_matches_oracle():
+    op, polys, lam, Z, pair = small_setup()
+    defl = M.Deflation(op, Z, lam, pair)
+    B = synth.random_block(op.n, 5, 21)
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        R = h.mpmc_project(B)
+    ref = K.left_right_projection(op, defl.Z, defl.U, B)[1]
+    assert np.linalg.norm(R - ref) < 1e-11 * np.linalg.norm(ref)
+    assert np.linalg.norm(defl.U.conj().T @ R) < 1e-10 * np.linalg.norm(B)
+
+
 # ---------------------------------------------------------------- errors
 def test_error_codes():
     with handle((2, 2, 2, 2)) as h:
