@@ -267,8 +267,11 @@ MPMC_API long long mpmc_launch_count(mpmc_handle h);
  * 0 selects the default (1, 64, 1).  mpmc_get_launch reports the current
  * shape and block width.  mpmc_autotune times short noise-started chains of
  * `steps` fused steps (the trace-mode kernel) for block widths up to max_nb
- * and the shapes above on this handle's lattice and precision, and keeps
- * the fastest per site and right-hand side (block width as mpmc_set_block).
+ * and the shapes above on this handle's lattice and precision, then (where
+ * MPMC_OPT_SWEEP_STENCIL is on and applies) the t-sweep kernel with t-segment
+ * lengths Lt, Lt/2, ... , and keeps the fastest per site and right-hand
+ * side (block width as mpmc_set_block; sweep on/off and segment length as
+ * the two options below).
  */
 MPMC_API int mpmc_set_launch(mpmc_handle h, int R, int bx, int sl);
 MPMC_API int mpmc_get_launch(mpmc_handle h, int* nb, int* R, int* bx, int* sl);
@@ -281,8 +284,19 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * the CUDA-core kernel.  Both use the same stored vectors zhat = hi + lo, so
  * the exact correction matches either way.  mpmc_get_option reports whether
  * the tensor-core path is in use (1) or not (0).
+ * MPMC_OPT_SWEEP_STENCIL (default 1): on FP32 / BF16S handles whose x, y, z
+ * extents are even (and block widths with 16-byte rows), every stencil step
+ * whose input is a stored block (all but the first step of a noise chain)
+ * runs the t-sweep kernel: a CTA walks t over a 2 x 2 x 2 block of sites and
+ * 32 right-hand sides with the block's spinor planes staged in shared memory
+ * by TMA.  Same arithmetic per site as the site-parallel kernel; only the
+ * order of the FP64 per-block dot sums differs.  mpmc_get_option reports
+ * whether it applies to the handle's current block width.
+ * MPMC_OPT_SWEEP_SEGMENT: t-extent walked by one CTA (0 = automatic, else
+ * 1 .. Lt); mpmc_get_option returns the length in effect.  mpmc_autotune
+ * sets both.
  */
-enum { MPMC_OPT_TENSOR_CORE_DEFLATION = 1 };
+enum { MPMC_OPT_TENSOR_CORE_DEFLATION = 1, MPMC_OPT_SWEEP_STENCIL = 2, MPMC_OPT_SWEEP_SEGMENT = 3 };
 MPMC_API int mpmc_set_option(mpmc_handle h, int option, int value);
 MPMC_API int mpmc_get_option(mpmc_handle h, int option, int* value);
 

@@ -254,7 +254,11 @@ __global__ void k_tc_reduce(int k, int nb, int Mpad, int Npad, int nsplit, const
     G2[idx] = make_double2(a2, a3);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+// ================================================================== host side
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -267,9 +271,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-}  // namespace
-
-// ================================================================== host side
 int tc_defl_layout(int V, int k, int* Mpad, int* Kpad) {
     *Mpad = ((k + BM - 1) / BM) * BM;
     *Kpad = ((24 * V + BK - 1) / BK) * BK;
@@ -284,7 +285,7 @@ void launch_split_bf16(int V, int k, int Mpad, int Kpad, const double* z, float*
 
 // Encode the TMA map of the two planes ([2 Mpad] rows x Kpad BF16, 128-byte swizzle, 64 x 128 boxes).
 bool tc_make_map(void* map, const void* planes, int Mpad, int Kpad) {
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)(2 * Mpad)};
     cuuint64_t strides[1] = {(cuuint64_t)Kpad * 2};

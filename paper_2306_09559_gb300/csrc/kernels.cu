@@ -361,15 +361,28 @@ LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R) {
     return c;
 }
 
-void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a0,
-                 const LaunchCfg& c, cudaStream_t s) {
-    StepArgs a = a0;
+void fill_floats(StepArgs& a) {
     for (int i = 0; i < 2; ++i) {
         a.alphaf[i] = (float)a.alpha[i];
         a.yaf[i] = (float)a.ya[i];
         a.ybf[i] = (float)a.yb[i];
     }
     a.kappaf = (float)a.kappa;
+}
+
+void fill_floats(OuterArgs& a) {
+    for (int i = 0; i < 2; ++i) {
+        a.alphaf[i] = (float)a.alpha[i];
+        a.betaf[i] = (float)a.beta[i];
+        a.gammaf[i] = (float)a.gamma[i];
+    }
+    a.kappaf = (float)a.kappa;
+}
+
+void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a0,
+                 const LaunchCfg& c, cudaStream_t s) {
+    StepArgs a = a0;
+    fill_floats(a);
     if (storage == ST_F64) step_f64(g, links, nb, ns, a, c, s);
     else if (storage == ST_F32) step_f32(g, links, nb, ns, a, c, s);
     else step_bf16(g, links, nb, ns, a, c, s);
@@ -378,12 +391,7 @@ void launch_step(int storage, const Geom& g, const void* links, int nb, const No
 void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const OuterArgs& a0,
                   const LaunchCfg& c, cudaStream_t s) {
     OuterArgs a = a0;
-    for (int i = 0; i < 2; ++i) {
-        a.alphaf[i] = (float)a.alpha[i];
-        a.betaf[i] = (float)a.beta[i];
-        a.gammaf[i] = (float)a.gamma[i];
-    }
-    a.kappaf = (float)a.kappa;
+    fill_floats(a);
     if (storage == ST_F64) outer_f64(g, links, nb, ns, a, c, s);
     else if (storage == ST_F32) outer_f32(g, links, nb, ns, a, c, s);
     else outer_bf16(g, links, nb, ns, a, c, s);

@@ -72,10 +72,30 @@ void outer_f64(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&
 void outer_f32(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 void outer_bf16(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 
+// FP32 copies of the coefficients (what the FP32 / BF16 kernels use)
+void fill_floats(StepArgs& a);
+void fill_floats(OuterArgs& a);
+
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                  const StepArgs& a, const LaunchCfg& cfg, cudaStream_t s);
 void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                   const OuterArgs& a, const LaunchCfg& cfg, cudaStream_t s);
+
+// t-sweep form of the step / outer kernels (stencil_sweep.cu): FP32 and
+// BF16 storage, even lx, ly, lz; the input block is read by TMA through a
+// tensor map made by sweep_make_map for that buffer.  Accumulator rows:
+// cfg.rows (one per site block and t-segment).
+struct SweepCfg {
+    int nblk, tiles, ts, nseg, rows;
+};
+bool sweep_supported(int storage, const Geom& g, int nb);
+SweepCfg sweep_config(const Geom& g, int nb, int ts);   // ts <= 0: automatic segment length
+size_t sweep_map_bytes();
+bool sweep_make_map(void* map, int storage, const void* base, int V, int nb);
+int launch_sweep_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a,
+                      const SweepCfg& c, const void* map, int* err, cudaStream_t s);
+int launch_sweep_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
+                       const OuterArgs& a, const SweepCfg& c, const void* map, int* err, cudaStream_t s);
 
 // out = scale * noise block (all nb columns)
 void launch_fill_noise(int storage, const Geom& g, int nb, const NoiseSpec& ns, const double scale[2],

@@ -38,6 +38,15 @@ struct Workspace {
     int acc_rows = 0;
     size_t acc_cap = 0;       // accumulator entries allocated per buffer
     LaunchCfg cfg{};
+    bool sweep = false;       // steps with a memory input use the t-sweep kernels
+    SweepCfg sw{};
+};
+
+// TMA tensor map of one input buffer of the t-sweep kernels
+struct SweepMap {
+    const void* p = nullptr;
+    int storage = -1, nb = 0, V = 0;
+    alignas(64) unsigned char m[128];
 };
 
 size_t storage_bytes(int st) { return st == ST_F64 ? 16 : (st == ST_F32 ? 8 : 4); }
@@ -88,6 +97,10 @@ struct mpmc_ctx {
     float* tc_part = nullptr;
     size_t tc_part_cap = 0;
     int* d_err = nullptr;         // device flag set by kernels whose bounded waits expired
+    // t-sweep stencil: option, t-segment length (0 automatic), tensor maps of input buffers
+    int use_sweep = 1;
+    int sweep_ts = 0;
+    std::vector<SweepMap> maps;
     // work
     int nb_user = 0;
     int tune_R = 1, tune_bx = 64, tune_sl = 1;   // launch shape of the stencil kernels
@@ -174,7 +187,10 @@ void free_ws(Workspace& w) {
 // Launch shape for the workspace's block; grows the accumulators if needed.
 int set_cfg(mpmc_ctx* h, Workspace& w) {
     w.cfg = chain_config(h->g, w.nb, h->tune_bx, h->tune_sl, h->tune_R);
-    w.acc_rows = w.cfg.gx;   // one accumulator row per site block
+    w.sweep = h->use_sweep && sweep_supported(w.storage, h->g, w.nb);
+    if (w.sweep) w.sw = sweep_config(h->g, w.nb, h->sweep_ts);
+    // one accumulator row per site block (k_step) or per site block and t-segment (sweep)
+    w.acc_rows = std::max(w.cfg.gx, w.sweep ? w.sw.rows : 0);
     const size_t need = (size_t)w.acc_rows * w.nb;
     if (need > w.acc_cap) {
         dev_free(w.acc_hi);
@@ -251,12 +267,53 @@ enum { PROF_STENCIL = 0, PROF_DEFLATION = 1, PROF_OTHER = 2 };
 
 double link_bytes(const mpmc_ctx* h, int st) { return (double)h->g.V * 36 * (st == ST_F64 ? 16 : 8); }
 
+// After a synchronisation: ETIMEOUT (and the flag cleared) if a kernel's
+// bounded wait on a TMA or tensor-core pipeline gave up.
+int device_flag(mpmc_ctx* h) {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (TMA / tensor-core pipeline)");
+    }
+    return MPMC_OK;
+}
+
+// Tensor map of a step input for the t-sweep kernels (made once per buffer and block shape).
+const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in) {
+    for (const SweepMap& m : h->maps)
+        if (m.p == in && m.storage == ws.storage && m.nb == ws.nb && m.V == h->g.V) return m.m;
+    SweepMap m;
+    if (!sweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb)) return nullptr;
+    m.p = in;
+    m.storage = ws.storage;
+    m.nb = ws.nb;
+    m.V = h->g.V;
+    if (h->maps.size() >= 64) h->maps.erase(h->maps.begin());
+    h->maps.push_back(m);
+    return h->maps.back().m;
+}
+
+// One stencil step on the workspace's launch shape: the t-sweep kernel when
+// the input is a memory block and the shape allows it, else k_step.
+int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
+    const void* map = (ws.sweep && a.in) ? sweep_map(h, ws, a.in) : nullptr;
+    if (map) {
+        if (launch_sweep_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.sw, map, h->d_err,
+                              h->stream))
+            return fail(h, MPMC_ECUDA, "t-sweep step launch failed");
+    } else {
+        launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
+    }
+    return MPMC_OK;
+}
+
 int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
     const int reads = (a.in ? 1 : 0) + (a.ymode == 2 ? 1 : 0);
     const int writes = 1 + (a.ymode ? 1 : 0);
     const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * (reads + writes) + link_bytes(h, ws.storage);
     if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
-    launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
+    if (int rc = step_launch(h, ws, a, ns)) return rc;
     if (int rc = prof_end(h)) return rc;
     LAUNCHED(1);
     return MPMC_OK;
@@ -265,7 +322,14 @@ int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) 
 int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
     const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
     if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
-    launch_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.cfg, h->stream);
+    const void* map = ws.sweep ? sweep_map(h, ws, o.in) : nullptr;
+    if (map) {
+        if (launch_sweep_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.sw, map, h->d_err,
+                               h->stream))
+            return fail(h, MPMC_ECUDA, "t-sweep outer launch failed");
+    } else {
+        launch_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.cfg, h->stream);
+    }
     if (int rc = prof_end(h)) return rc;
     LAUNCHED(1);
     return MPMC_OK;
@@ -1042,6 +1106,7 @@ int mpmc_apply_op(mpmc_handle h, const double* X, double* Y, int nrhs, int on_de
     }
     if (!on_device) CK(cudaMemcpyAsync(Y, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (int rc = device_flag(h)) return rc;
     return prof_collect(h);
 }
 
@@ -1094,6 +1159,7 @@ int mpmc_apply_poly(mpmc_handle h, int index, const double* B, double* X, int nr
     }
     if (!on_device) CK(cudaMemcpyAsync(X, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (int rc = device_flag(h)) return rc;
     return prof_collect(h);
 }
 
@@ -1174,14 +1240,7 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
     CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (int rc = prof_collect(h)) return rc;
-    {
-        int flag = 0;
-        CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (flag) {
-            CK(cudaMemset(h->d_err, 0, sizeof(int)));
-            return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (tensor-core deflation pipeline)");
-        }
-    }
+    if (int rc = device_flag(h)) return rc;
     for (size_t i = 0; i < need; ++i)
         if (!std::isfinite(hs[i].x) || !std::isfinite(hs[i].y)) return fail(h, MPMC_ENONFINITE, "non-finite sample");
     for (int l = 0; l < L; ++l) {
@@ -1375,51 +1434,76 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    const bool prof = h->prof;
+    h->prof = false;
     double best = INFINITY;
-    int bnb = 0, bR = 1, bbx = 64, bsl = 1;
+    int bnb = 0, bR = 1, bbx = 64, bsl = 1, bsweep = 0, bts = 0;
     const int nbs[] = {16, 32, 64, 128, 256, 512, 1024};
     const int bxs[] = {32, 64};
     const int sls[] = {1, 2};
     const NoiseSpec ns{0x5eedULL, 0, 0};
     int rc = MPMC_OK;
+    // time one candidate: a noise-started chain of `steps` fused steps
+    auto trial = [&](int nb) -> int {
+        if ((rc = ensure_ws(h, h->ws, h->storage, nb))) return rc;
+        Workspace& ws = h->ws;
+        auto chain = [&]() -> int {
+            for (int j = 0; j < steps; ++j) {
+                StepArgs a{};
+                a.in = j == 0 ? nullptr : ws.w[(j - 1) % 2];
+                a.out = ws.w[j % 2];
+                a.dot = true;
+                setc(a.alpha, 0.5);
+                a.kappa = h->kappa;
+                setc(a.dot_w, 1.0);
+                a.acc = ws.acc_hi;
+                if (int r = step_launch(h, ws, a, ns)) return r;
+            }
+            return cuda_check(h, cudaGetLastError(), "autotune launch");
+        };
+        if ((rc = chain())) return rc;   // warm-up
+        if ((rc = cuda_check(h, cudaEventRecord(e0, h->stream), "event"))) return rc;
+        if ((rc = chain())) return rc;
+        if ((rc = cuda_check(h, cudaEventRecord(e1, h->stream), "event"))) return rc;
+        if ((rc = cuda_check(h, cudaEventSynchronize(e1), "event"))) return rc;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->launches += 2 * steps;
+        const double per = ms / ((double)steps * nb * h->g.V);
+        if (per < best) {
+            best = per; bnb = nb; bR = ws.cfg.R; bbx = h->tune_bx; bsl = h->tune_sl;
+            bsweep = ws.sweep ? 1 : 0; bts = h->sweep_ts;
+        }
+        return MPMC_OK;
+    };
+    const int user_sweep = h->use_sweep;
     for (int nb : nbs) {
         if (nb > max_nb) break;
         // the six work vectors of a block must stay within ~24 GB
         if ((size_t)h->g.V * 12 * storage_bytes(h->storage) * 7 * nb > ((size_t)24 << 30)) break;
+        // site-parallel kernel shapes
+        h->use_sweep = 0;
         for (int R = 1; R <= 2 && !rc; ++R)
             for (int bx : bxs)
                 for (int sl : sls) {
+                    if (rc) break;
                     if (nb / R < bx && bx != bxs[0]) continue;
                     h->tune_R = R; h->tune_bx = bx; h->tune_sl = sl;
-                    if ((rc = ensure_ws(h, h->ws, h->storage, nb))) break;
-                    Workspace& ws = h->ws;
-                    auto chain = [&]() -> int {
-                        for (int j = 0; j < steps; ++j) {
-                            StepArgs a{};
-                            a.in = j == 0 ? nullptr : ws.w[(j - 1) % 2];
-                            a.out = ws.w[j % 2];
-                            a.dot = true;
-                            setc(a.alpha, 0.5);
-                            a.kappa = h->kappa;
-                            setc(a.dot_w, 1.0);
-                            a.acc = ws.acc_hi;
-                            launch_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.cfg, h->stream);
-                        }
-                        return cuda_check(h, cudaGetLastError(), "autotune launch");
-                    };
-                    if ((rc = chain())) break;                 // warm-up
-                    if ((rc = cuda_check(h, cudaEventRecord(e0, h->stream), "event"))) break;
-                    if ((rc = chain())) break;
-                    if ((rc = cuda_check(h, cudaEventRecord(e1, h->stream), "event"))) break;
-                    if ((rc = cuda_check(h, cudaEventSynchronize(e1), "event"))) break;
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    h->launches += 2 * steps;
-                    const double per = ms / ((double)steps * nb * h->g.V);
-                    if (per < best) { best = per; bnb = nb; bR = ws.cfg.R; bbx = bx; bsl = sl; }
+                    trial(nb);
                 }
+        // t-sweep segment lengths (first step keeps the best site-parallel shape of this width)
+        if (!rc && user_sweep && sweep_supported(h->storage, h->g, nb)) {
+            h->use_sweep = 1;
+            h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
+            for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
+                h->sweep_ts = ts;
+                trial(nb);
+            }
+        }
         if (rc) break;
     }
+    h->use_sweep = user_sweep;
+    h->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -1428,6 +1512,8 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     h->tune_R = bR;
     h->tune_bx = bbx;
     h->tune_sl = bsl;
+    h->use_sweep = bsweep;
+    h->sweep_ts = bsweep ? bts : 0;
     return ensure_ws(h, h->ws, h->storage, bnb);
 }
 
@@ -1436,6 +1522,13 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
     switch (option) {
         case MPMC_OPT_TENSOR_CORE_DEFLATION:
             h->use_tc = value != 0;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_STENCIL:
+            h->use_sweep = value != 0;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_SEGMENT:
+            if (value < 0 || value > h->g.lt) return fail(h, MPMC_EINVAL, "t-segment length out of range");
+            h->sweep_ts = value;
             return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");
@@ -1447,6 +1540,12 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
     switch (option) {
         case MPMC_OPT_TENSOR_CORE_DEFLATION:
             *value = (h->use_tc && h->tc_ready && h->storage != ST_F64) ? 1 : 0;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_STENCIL:
+            *value = (h->use_sweep && sweep_supported(h->storage, h->g, h->ws.nb > 0 ? h->ws.nb : default_nb(h))) ? 1 : 0;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_SEGMENT:
+            *value = sweep_config(h->g, h->ws.nb > 0 ? h->ws.nb : default_nb(h), h->sweep_ts).ts;
             return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");
@@ -1486,13 +1585,7 @@ int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int first, int 
     CK(cudaMemcpyAsync(G1, h->G1, cnt * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(G2, h->G2, cnt * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    int flag = 0;
-    CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) {
-        CK(cudaMemset(h->d_err, 0, sizeof(int)));
-        return fail(h, MPMC_ETIMEOUT, "a bounded device wait gave up (tensor-core deflation pipeline)");
-    }
-    return MPMC_OK;
+    return device_flag(h);
 }
 
 int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {

@@ -5,10 +5,15 @@
 // returns.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace mpmc {
+
+// cuTensorMapEncodeTiled from the driver entry point table (defl_tc.cu).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

@@ -74,6 +74,8 @@ _SIGS = {
 }
 
 OPT_TENSOR_CORE_DEFLATION = 1
+OPT_SWEEP_STENCIL = 2
+OPT_SWEEP_SEGMENT = 3
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
