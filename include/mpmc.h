@@ -268,7 +268,7 @@ MPMC_API long long mpmc_launch_count(mpmc_handle h);
  * shape and block width.  mpmc_autotune times short noise-started chains of
  * `steps` fused steps (the trace-mode kernel) for block widths up to max_nb
  * and the shapes above on this handle's lattice and precision, then (where
- * MPMC_OPT_SWEEP_STENCIL is on and applies) the t-sweep kernel with t-segment
+ * the options below allow) the issue-lean kernels and the t-sweep with t-segment
  * lengths Lt, Lt/2, ... , and keeps the fastest per site and right-hand
  * side (block width as mpmc_set_block; sweep on/off and segment length as
  * the two options below).
@@ -284,19 +284,39 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * the CUDA-core kernel.  Both use the same stored vectors zhat = hi + lo, so
  * the exact correction matches either way.  mpmc_get_option reports whether
  * the tensor-core path is in use (1) or not (0).
- * MPMC_OPT_SWEEP_STENCIL (default 1): on FP32 / BF16S handles whose x, y, z
- * extents are even (and block widths with 16-byte rows), every stencil step
+ * MPMC_OPT_FAST_STENCIL (default 1): on FP32 / BF16S handles with block
+ * widths 16, 32, 64, ..., 1024, the trace-mode and composite stencil steps
+ * run the issue-lean kernels: packed FP32x2 arithmetic on (re, im) pairs,
+ * links expanded once per field to (re, re, im, im) pairs (16 bytes per
+ * link element), compile-time block width, Z4 symbols from a per-block word
+ * table (4 bytes per site and right-hand side) and a table-driven noise
+ * dot.  Same per-component FMA rounding as the site-parallel kernel; the
+ * grouping of the hopping sums differs (FP32 rounding level).
+ * MPMC_OPT_FAST_SITES: sites per thread of those kernels (1 .. 16, default
+ * 1).  mpmc_get_option(MPMC_OPT_FAST_STENCIL) reports whether they apply to
+ * the handle's current block width.
+ * MPMC_OPT_SWEEP_STENCIL (default 1): t-sweep form of the stencil steps
  * whose input is a stored block (all but the first step of a noise chain)
- * runs the t-sweep kernel: a CTA walks t over a 2 x 2 x 2 block of sites and
- * 32 right-hand sides with the block's spinor planes staged in shared memory
- * by TMA.  Same arithmetic per site as the site-parallel kernel; only the
- * order of the FP64 per-block dot sums differs.  mpmc_get_option reports
- * whether it applies to the handle's current block width.
+ * on handles whose x, y, z extents are even: a CTA walks t over a 2 x 2 x 2
+ * block of sites and a tile of right-hand sides, with the block's spinor
+ * planes staged in shared memory by TMA, and reads only the three
+ * neighbours outside the block from global memory.  1: for the issue-lean
+ * kernels (where MPMC_OPT_FAST_STENCIL applies); 2: also for the
+ * site-parallel arithmetic on other FP32 / BF16S block widths (with 16-byte
+ * rows).  Same arithmetic per site as the non-sweep kernel; only the order
+ * of the FP64 per-block dot sums differs.  mpmc_get_option reports 1 or 2
+ * where a sweep applies to the handle's current block width, else 0.
  * MPMC_OPT_SWEEP_SEGMENT: t-extent walked by one CTA (0 = automatic, else
  * 1 .. Lt); mpmc_get_option returns the length in effect.  mpmc_autotune
- * sets both.
+ * sets all four options.
  */
-enum { MPMC_OPT_TENSOR_CORE_DEFLATION = 1, MPMC_OPT_SWEEP_STENCIL = 2, MPMC_OPT_SWEEP_SEGMENT = 3 };
+enum {
+    MPMC_OPT_TENSOR_CORE_DEFLATION = 1,
+    MPMC_OPT_SWEEP_STENCIL = 2,
+    MPMC_OPT_SWEEP_SEGMENT = 3,
+    MPMC_OPT_FAST_STENCIL = 4,
+    MPMC_OPT_FAST_SITES = 5
+};
 MPMC_API int mpmc_set_option(mpmc_handle h, int option, int value);
 MPMC_API int mpmc_get_option(mpmc_handle h, int option, int* value);
 

@@ -81,13 +81,52 @@ void launch_step(int storage, const Geom& g, const void* links, int nb, const No
 void launch_outer(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                   const OuterArgs& a, const LaunchCfg& cfg, cudaStream_t s);
 
+// Shape of a t-sweep launch: site blocks, right-hand-side tiles, t-segment
+// length and count, accumulator rows (blocks x segments).
+struct SweepCfg {
+    int nblk, tiles, ts, nseg, rows;
+};
+
+// Issue-lean FP32-arithmetic stencil kernels (stencil_fast.cuh): FP32 /
+// BF16 storage, block widths NB in {16, 32, 64, 128, 256, 512, 1024}
+// (compile-time row stride), links expanded to broadcast pairs, Z4 symbols
+// from a per-block word table.  Same step / outer semantics as StepArgs /
+// OuterArgs (ymode 0 only).  Accumulator rows: ceil(V / (sites per CTA * sl)).
+struct FastArgs {
+    const void* in;          // input block (unused when the input is the noise)
+    void* out;               // step: output;  outer: w_out
+    const void* w;           // outer: w
+    void* y;                 // outer: y
+    const uint32_t* words;   // Z4 words [V][NB] of the noise block
+    const float4* Ue;        // expanded links [V][4][9] (re, re, im, im)
+    double2* acc;
+    double dot_w[2];
+    float alpha[2], beta[2], gamma[2], kappa;
+    int lx, ly, lz, lt, V, bc_t, sl;
+    unsigned long long mx, my, mz;   // floor(2^64 / extent) + 1
+};
+bool fast_supported(int storage, int nb);
+int fast_sites_per_cta(int nb);
+// kind: 0 step, 1 step + dot, 2 step from the noise + dot, 3 outer, 4 outer + dot
+int launch_fast(int storage, int nb, int kind, const FastArgs& a, int gx, cudaStream_t s);
+void fast_geometry(const Geom& g, FastArgs& a);
+// t-sweep form of the issue-lean kernels (stencil_fsweep.cu): kinds 0, 1,
+// 3, 4; even lx, ly, lz; the input block read by TMA through a tensor map
+// made by fsweep_make_map; accumulator rows cfg.rows.
+bool fsweep_supported(int storage, const Geom& g, int nb);
+SweepCfg fsweep_config(const Geom& g, int nb, int ts);
+bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb);
+int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepCfg& c, const void* map, int* err,
+                  cudaStream_t s);
+// Z4 words of a noise block: words[site][col] = Philox word 0 of (j0 + col, site, level)
+void launch_noise_words(const Geom& g, int nb, const NoiseSpec& ns, uint32_t* words, cudaStream_t s);
+// expanded links (re, re, im, im) in float from complex-double [mu][site][3][3]
+void launch_links_expanded(int V, const double* src, float4* dst, cudaStream_t s);
+
 // t-sweep form of the step / outer kernels (stencil_sweep.cu): FP32 and
 // BF16 storage, even lx, ly, lz; the input block is read by TMA through a
 // tensor map made by sweep_make_map for that buffer.  Accumulator rows:
 // cfg.rows (one per site block and t-segment).
-struct SweepCfg {
-    int nblk, tiles, ts, nseg, rows;
-};
 bool sweep_supported(int storage, const Geom& g, int nb);
 SweepCfg sweep_config(const Geom& g, int nb, int ts);   // ts <= 0: automatic segment length
 size_t sweep_map_bytes();

@@ -38,14 +38,21 @@ struct Workspace {
     int acc_rows = 0;
     size_t acc_cap = 0;       // accumulator entries allocated per buffer
     LaunchCfg cfg{};
-    bool sweep = false;       // steps with a memory input use the t-sweep kernels
+    bool sweep = false;       // steps with a memory input use the k_sweep kernels
     SweepCfg sw{};
+    bool fast = false;        // ymode-0 steps and outer steps use the issue-lean kernels
+    int fast_gx = 0;          // their CTA count along the sites
+    bool fsweep = false;      // ... in their t-sweep form (steps with a memory input)
+    SweepCfg fsw{};
+    uint32_t* words = nullptr;        // Z4 words of the current noise block
+    NoiseSpec words_ns{0, 0, 0};
+    bool words_ok = false;
 };
 
 // TMA tensor map of one input buffer of the t-sweep kernels
 struct SweepMap {
     const void* p = nullptr;
-    int storage = -1, nb = 0, V = 0;
+    int storage = -1, nb = 0, V = 0, kind = 0;   // kind 0: k_sweep boxes, 1: k_fsweep boxes
     alignas(64) unsigned char m[128];
 };
 
@@ -62,6 +69,7 @@ struct mpmc_ctx {
     cudaStream_t stream = nullptr;
     void* links64 = nullptr;      // [site][mu][3][3] complex double
     void* links32 = nullptr;      // same in float (FP32 / BF16S handles)
+    float4* links_ex = nullptr;   // float links expanded to (re, re, im, im) for the issue-lean kernels
     PolyDef polys[MPMC_MAX_POLYS];
     // deflation
     int k = 0;
@@ -98,8 +106,10 @@ struct mpmc_ctx {
     size_t tc_part_cap = 0;
     int* d_err = nullptr;         // device flag set by kernels whose bounded waits expired
     // t-sweep stencil: option, t-segment length (0 automatic), tensor maps of input buffers
-    int use_sweep = 1;
+    int use_sweep = 1;            // 1: t-sweep form of the issue-lean kernels; 2: also the k_sweep kernels
     int sweep_ts = 0;
+    int use_fast = 1;             // issue-lean kernels (FP32 / BF16S, block widths 16 .. 1024)
+    int fast_sl = 1;              // sites per thread of the issue-lean kernels
     std::vector<SweepMap> maps;
     // work
     int nb_user = 0;
@@ -179,6 +189,8 @@ void free_ws(Workspace& w) {
     dev_free(w.x);
     dev_free(w.acc_hi);
     dev_free(w.acc_lo);
+    dev_free(w.words);
+    w.words_ok = false;
     w.acc_cap = 0;
     w.nb = 0;
     w.storage = -1;
@@ -187,10 +199,18 @@ void free_ws(Workspace& w) {
 // Launch shape for the workspace's block; grows the accumulators if needed.
 int set_cfg(mpmc_ctx* h, Workspace& w) {
     w.cfg = chain_config(h->g, w.nb, h->tune_bx, h->tune_sl, h->tune_R);
-    w.sweep = h->use_sweep && sweep_supported(w.storage, h->g, w.nb);
+    w.fast = h->use_fast && fast_supported(w.storage, w.nb);
+    if (w.fast) {
+        const int per = fast_sites_per_cta(w.nb) * h->fast_sl;
+        w.fast_gx = (h->g.V + per - 1) / per;
+    }
+    w.fsweep = w.fast && h->use_sweep && fsweep_supported(w.storage, h->g, w.nb);
+    if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts);
+    w.sweep = !w.fast && h->use_sweep == 2 && sweep_supported(w.storage, h->g, w.nb);
     if (w.sweep) w.sw = sweep_config(h->g, w.nb, h->sweep_ts);
     // one accumulator row per site block (k_step) or per site block and t-segment (sweep)
-    w.acc_rows = std::max(w.cfg.gx, w.sweep ? w.sw.rows : 0);
+    w.acc_rows = std::max(std::max(w.cfg.gx, w.sweep ? w.sw.rows : 0),
+                          std::max(w.fast ? w.fast_gx : 0, w.fsweep ? w.fsw.rows : 0));
     const size_t need = (size_t)w.acc_rows * w.nb;
     if (need > w.acc_cap) {
         dev_free(w.acc_hi);
@@ -213,6 +233,8 @@ int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
     if (int rc = dev_alloc(h, &w.y, vb)) return rc;
     if (int rc = dev_alloc(h, &w.r, vb)) return rc;
     if (int rc = dev_alloc(h, &w.x, vb)) return rc;
+    if (int rc = dev_alloc(h, &w.words, sizeof(uint32_t) * (size_t)h->g.V * nb)) return rc;
+    w.words_ok = false;
     // padding columns must hold finite values: clear everything once
     for (auto& p : w.w) CK(cudaMemsetAsync(p, 0, vb, h->stream));
     CK(cudaMemsetAsync(w.y, 0, vb, h->stream));
@@ -279,25 +301,71 @@ int device_flag(mpmc_ctx* h) {
     return MPMC_OK;
 }
 
-// Tensor map of a step input for the t-sweep kernels (made once per buffer and block shape).
-const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in) {
+// Tensor map of a step input for the t-sweep kernels (made once per buffer, block shape and box).
+const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in, int kind) {
     for (const SweepMap& m : h->maps)
-        if (m.p == in && m.storage == ws.storage && m.nb == ws.nb && m.V == h->g.V) return m.m;
+        if (m.p == in && m.storage == ws.storage && m.nb == ws.nb && m.V == h->g.V && m.kind == kind) return m.m;
     SweepMap m;
-    if (!sweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb)) return nullptr;
+    const bool made = kind ? fsweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb)
+                           : sweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb);
+    if (!made) return nullptr;
     m.p = in;
     m.storage = ws.storage;
     m.nb = ws.nb;
     m.V = h->g.V;
+    m.kind = kind;
     if (h->maps.size() >= 64) h->maps.erase(h->maps.begin());
     h->maps.push_back(m);
     return h->maps.back().m;
 }
 
-// One stencil step on the workspace's launch shape: the t-sweep kernel when
-// the input is a memory block and the shape allows it, else k_step.
+// Z4 word table of the noise block `ns` for the issue-lean kernels (made when the block changes).
+int ensure_words(mpmc_ctx* h, Workspace& ws, const NoiseSpec& ns) {
+    if (ws.words_ok && ws.words_ns.seed == ns.seed && ws.words_ns.level == ns.level && ws.words_ns.j0 == ns.j0)
+        return MPMC_OK;
+    launch_noise_words(h->g, ws.nb, ns, ws.words, h->stream);
+    LAUNCHED(1);
+    ws.words_ns = ns;
+    ws.words_ok = true;
+    return MPMC_OK;
+}
+
+FastArgs fast_args(const mpmc_ctx* h, const Workspace& ws, double kappa) {
+    FastArgs f{};
+    fast_geometry(h->g, f);
+    f.Ue = h->links_ex;
+    f.words = ws.words;
+    f.sl = h->fast_sl;
+    f.kappa = (float)kappa;
+    return f;
+}
+
+// One stencil step on the workspace's launch shape: the issue-lean kernels
+// (t-sweep form when the input is a stored block and the shape allows it)
+// for ymode-0 steps of FP32 / BF16S blocks of the compiled widths, else the
+// site-parallel k_step (or k_sweep when selected).
 int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
-    const void* map = (ws.sweep && a.in) ? sweep_map(h, ws, a.in) : nullptr;
+    if (ws.fast && a.ymode == 0 && !a.op_only && (a.in || a.dot)) {
+        const int kind = a.in ? (a.dot ? 1 : 0) : 2;
+        if (kind) if (int rc = ensure_words(h, ws, ns)) return rc;
+        FastArgs f = fast_args(h, ws, a.kappa);
+        f.in = a.in;
+        f.out = a.out;
+        f.acc = a.acc;
+        f.dot_w[0] = a.dot_w[0];
+        f.dot_w[1] = a.dot_w[1];
+        f.alpha[0] = (float)a.alpha[0];
+        f.alpha[1] = (float)a.alpha[1];
+        const void* fmap = (ws.fsweep && kind < 2) ? sweep_map(h, ws, a.in, 1) : nullptr;
+        if (fmap) {
+            if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream))
+                return fail(h, MPMC_ECUDA, "issue-lean t-sweep step launch failed");
+        } else if (launch_fast(ws.storage, ws.nb, kind, f, ws.fast_gx, h->stream)) {
+            return fail(h, MPMC_ECUDA, "issue-lean step launch failed");
+        }
+        return MPMC_OK;
+    }
+    const void* map = (ws.sweep && a.in) ? sweep_map(h, ws, a.in, 0) : nullptr;
     if (map) {
         if (launch_sweep_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.sw, map, h->d_err,
                               h->stream))
@@ -322,8 +390,30 @@ int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) 
 int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
     const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
     if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
-    const void* map = ws.sweep ? sweep_map(h, ws, o.in) : nullptr;
-    if (map) {
+    const void* map = ws.sweep ? sweep_map(h, ws, o.in, 0) : nullptr;
+    if (ws.fast) {
+        if (o.dot) if (int rc = ensure_words(h, ws, ns)) return rc;
+        FastArgs f = fast_args(h, ws, o.kappa);
+        f.in = o.in;
+        f.w = o.w;
+        f.out = o.wout;
+        f.y = o.y;
+        f.acc = o.acc;
+        f.dot_w[0] = o.dot_w[0];
+        f.dot_w[1] = o.dot_w[1];
+        for (int i = 0; i < 2; ++i) {
+            f.alpha[i] = (float)o.alpha[i];
+            f.beta[i] = (float)o.beta[i];
+            f.gamma[i] = (float)o.gamma[i];
+        }
+        const void* fmap = ws.fsweep ? sweep_map(h, ws, o.in, 1) : nullptr;
+        if (fmap) {
+            if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream))
+                return fail(h, MPMC_ECUDA, "issue-lean t-sweep outer launch failed");
+        } else if (launch_fast(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fast_gx, h->stream)) {
+            return fail(h, MPMC_ECUDA, "issue-lean outer launch failed");
+        }
+    } else if (map) {
         if (launch_sweep_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.sw, map, h->d_err,
                                h->stream))
             return fail(h, MPMC_ECUDA, "t-sweep outer launch failed");
@@ -907,6 +997,8 @@ int mpmc_create(mpmc_handle* out, const int dims[4], const double* links, double
     if (h->storage != ST_F64) {
         if ((rc = dev_alloc(h, &h->links32, nl * 8))) { dev_free(staging); return bail(rc); }
         launch_links(ST_F32, h->g.V, staging, h->links32, h->stream);
+        if ((rc = dev_alloc(h, &h->links_ex, nl * 16))) { dev_free(staging); return bail(rc); }
+        launch_links_expanded(h->g.V, staging, h->links_ex, h->stream);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         dev_free(staging);
@@ -925,6 +1017,7 @@ int mpmc_destroy(mpmc_handle h) {
     free_deflation(h);
     dev_free(h->links64);
     dev_free(h->links32);
+    dev_free(h->links_ex);
     dev_free(h->samples);
     dev_free(h->io);
     dev_free(h->kr_part);
@@ -1402,7 +1495,8 @@ int mpmc_set_links(mpmc_handle h, const double* links) {
     h->proj_ready = false;   // A Z changes with the links
     if (h->links32) {
         launch_links(ST_F32, h->g.V, h->io, h->links32, h->stream);
-        LAUNCHED(1);
+        launch_links_expanded(h->g.V, h->io, h->links_ex, h->stream);
+        LAUNCHED(2);
     }
     CK(cudaStreamSynchronize(h->stream));
     return MPMC_OK;
@@ -1437,7 +1531,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     const bool prof = h->prof;
     h->prof = false;
     double best = INFINITY;
-    int bnb = 0, bR = 1, bbx = 64, bsl = 1, bsweep = 0, bts = 0;
+    int bnb = 0, bR = 1, bbx = 64, bsl = 1, bsweep = 0, bts = 0, bfast = 0, bfsl = 1;
     const int nbs[] = {16, 32, 64, 128, 256, 512, 1024};
     const int bxs[] = {32, 64};
     const int sls[] = {1, 2};
@@ -1472,17 +1566,19 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         const double per = ms / ((double)steps * nb * h->g.V);
         if (per < best) {
             best = per; bnb = nb; bR = ws.cfg.R; bbx = h->tune_bx; bsl = h->tune_sl;
-            bsweep = ws.sweep ? 1 : 0; bts = h->sweep_ts;
+            bsweep = ws.fsweep ? 1 : (ws.sweep ? 2 : 0); bts = h->sweep_ts;
+            bfast = ws.fast ? 1 : 0; bfsl = h->fast_sl;
         }
         return MPMC_OK;
     };
-    const int user_sweep = h->use_sweep;
+    const int user_sweep = h->use_sweep, user_fast = h->use_fast;
     for (int nb : nbs) {
         if (nb > max_nb) break;
         // the six work vectors of a block must stay within ~24 GB
         if ((size_t)h->g.V * 12 * storage_bytes(h->storage) * 7 * nb > ((size_t)24 << 30)) break;
         // site-parallel kernel shapes
         h->use_sweep = 0;
+        h->use_fast = 0;
         for (int R = 1; R <= 2 && !rc; ++R)
             for (int bx : bxs)
                 for (int sl : sls) {
@@ -1491,18 +1587,40 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                     h->tune_R = R; h->tune_bx = bx; h->tune_sl = sl;
                     trial(nb);
                 }
-        // t-sweep segment lengths (first step keeps the best site-parallel shape of this width)
-        if (!rc && user_sweep && sweep_supported(h->storage, h->g, nb)) {
-            h->use_sweep = 1;
-            h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
+        h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
+        // issue-lean kernels: sites per thread, then their t-sweep form per segment length
+        if (!rc && user_fast && fast_supported(h->storage, nb)) {
+            h->use_fast = 1;
+            for (int fsl : {1, 2, 4}) {
+                if (rc) break;
+                h->fast_sl = fsl;
+                trial(nb);
+            }
+            if (user_sweep && fsweep_supported(h->storage, h->g, nb)) {
+                h->use_sweep = 1;
+                h->fast_sl = bfast ? bfsl : 1;
+                for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
+                    h->sweep_ts = ts;
+                    trial(nb);
+                }
+                h->use_sweep = 0;
+            }
+            h->use_fast = 0;
+        }
+        // k_sweep segment lengths (only when asked for; first step keeps the best site-parallel shape)
+        if (!rc && user_sweep == 2 && !(user_fast && fast_supported(h->storage, nb)) &&
+            sweep_supported(h->storage, h->g, nb)) {
+            h->use_sweep = 2;
             for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
                 h->sweep_ts = ts;
                 trial(nb);
             }
+            h->use_sweep = 0;
         }
         if (rc) break;
     }
     h->use_sweep = user_sweep;
+    h->use_fast = user_fast;
     h->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1514,6 +1632,8 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     h->tune_sl = bsl;
     h->use_sweep = bsweep;
     h->sweep_ts = bsweep ? bts : 0;
+    h->use_fast = bfast;
+    h->fast_sl = bfast ? bfsl : 1;
     return ensure_ws(h, h->ws, h->storage, bnb);
 }
 
@@ -1524,16 +1644,28 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->use_tc = value != 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            h->use_sweep = value != 0;
+            if (value < 0 || value > 2) return fail(h, MPMC_EINVAL, "sweep option is 0, 1 or 2");
+            h->use_sweep = value;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
             if (value < 0 || value > h->g.lt) return fail(h, MPMC_EINVAL, "t-segment length out of range");
             h->sweep_ts = value;
             return MPMC_OK;
+        case MPMC_OPT_FAST_STENCIL:
+            h->use_fast = value != 0;
+            return MPMC_OK;
+        case MPMC_OPT_FAST_SITES:
+            if (value < 1 || value > 16) return fail(h, MPMC_EINVAL, "sites per thread out of range");
+            h->fast_sl = value;
+            return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");
     }
 }
+
+namespace {
+int cur_nb(const mpmc_ctx* h) { return h->ws.nb > 0 ? h->ws.nb : default_nb(h); }
+}  // namespace
 
 int mpmc_get_option(mpmc_handle h, int option, int* value) {
     if (!h || !value) return MPMC_EINVAL;
@@ -1542,10 +1674,21 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
             *value = (h->use_tc && h->tc_ready && h->storage != ST_F64) ? 1 : 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            *value = (h->use_sweep && sweep_supported(h->storage, h->g, h->ws.nb > 0 ? h->ws.nb : default_nb(h))) ? 1 : 0;
+            if (h->use_fast && fast_supported(h->storage, cur_nb(h)))
+                *value = (h->use_sweep && fsweep_supported(h->storage, h->g, cur_nb(h))) ? 1 : 0;
+            else
+                *value = (h->use_sweep == 2 && sweep_supported(h->storage, h->g, cur_nb(h))) ? 2 : 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
-            *value = sweep_config(h->g, h->ws.nb > 0 ? h->ws.nb : default_nb(h), h->sweep_ts).ts;
+            *value = (h->use_fast && fsweep_supported(h->storage, h->g, cur_nb(h)))
+                         ? fsweep_config(h->g, cur_nb(h), h->sweep_ts).ts
+                         : sweep_config(h->g, cur_nb(h), h->sweep_ts).ts;
+            return MPMC_OK;
+        case MPMC_OPT_FAST_STENCIL:
+            *value = (h->use_fast && fast_supported(h->storage, cur_nb(h))) ? 1 : 0;
+            return MPMC_OK;
+        case MPMC_OPT_FAST_SITES:
+            *value = h->fast_sl;
             return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");

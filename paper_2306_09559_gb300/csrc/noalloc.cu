@@ -22,7 +22,7 @@ namespace {
 // process exits.  In host code `g_scratch` is only a host-side stand-in for
 // the symbol, never a device address: its device address is looked up once
 // per device with cudaGetSymbolAddress and that pointer is what the kernels get.
-__device__ __align__(256) unsigned char g_scratch[MPMC_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_scratch[MPMC_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 128;
 void* g_scratch_dev[kMaxDevices] = {};

@@ -76,6 +76,8 @@ _SIGS = {
 OPT_TENSOR_CORE_DEFLATION = 1
 OPT_SWEEP_STENCIL = 2
 OPT_SWEEP_SEGMENT = 3
+OPT_FAST_STENCIL = 4
+OPT_FAST_SITES = 5
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20
