@@ -373,11 +373,28 @@ def gpu_arm(args):
     avg_ms = st_ms / max(st_n, 1)
     bytes_per_launch = st_bytes / max(st_n, 1)
     achieved_gbs = bytes_per_launch / (avg_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": achieved_gbs / hbm, "traffic": args.traffic, "kernel": "k_step/k_outer (fused stencil step)",
-                "peak_source": src, "avg_launch_ms": avg_ms, "launches": st_n,
-                "share_of_step": st_ms / t_local if t_local else None,
-                "algorithmic_bytes_per_launch": bytes_per_launch}
+    # FP32 pipe: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock, against the
+    # algorithmic flops of one step per site and right-hand side
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    flops_per_launch = FLOPS_PER_SITE_RHS_STEP * float(np.prod(wl.dims)) * block
+    achieved_tflops = flops_per_launch / (avg_ms / 1000.0) / 1e12
+    t_hbm, t_alu = bytes_per_launch / (hbm * 1e9), flops_per_launch / (alu_peak * 1e12)
+    fast, sweep = hm.mpmc_get_option(G.OPT_FAST_STENCIL), hm.mpmc_get_option(G.OPT_SWEEP_STENCIL)
+    # step classes: 1 dotted steps, 2 undotted inner steps, 4 outer steps of composite chains
+    kernel = (f"fused stencil steps: issue-lean k_fast/k_fsweep for class mask {fast} "
+              f"(t-sweep mask {sweep & fast & 7}), site-parallel k_step/k_outer"
+              f"{' (k_sweep form)' if sweep & 8 else ''} for the others")
+    alu = {"achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak,
+           "flops_per_launch": flops_per_launch, "peak_source": "unit counts x max SM clock"}
+    if args.precision != "fp64" and t_alu > t_hbm:
+        # BF16-stored spinors: the FP32 arithmetic floor lies above the HBM floor
+        roofline = {"bound": "alu", **alu, "traffic": args.traffic, "hbm_frac": achieved_gbs / hbm}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "traffic": args.traffic, "alu": alu}
+    roofline.update({"kernel": kernel, "hbm_peak_source": src, "avg_launch_ms": avg_ms, "launches": st_n,
+                     "share_of_step": st_ms / t_local if t_local else None,
+                     "algorithmic_bytes_per_launch": bytes_per_launch})
 
     cpu = None
     if oracle_proc is not None:
@@ -402,7 +419,10 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": wl.describe(), "lattice": "x".join(map(str, wl.dims)),
                        "noises_per_level": wl.nsamples, "levels": [list(x) for x in wl.levels],
-                       "deflation_k": wl.k, "nrhs_per_launch": block, "launch_shape": launch, "l2": "flushed before every step (256 MB write)",
+                       "deflation_k": wl.k, "nrhs_per_launch": block, "launch_shape": launch,
+                       "stencil_options": {"fast": fast, "sweep": sweep,
+                                           "segment": hm.mpmc_get_option(G.OPT_SWEEP_SEGMENT),
+                                           "fast_sites": hm.mpmc_get_option(G.OPT_FAST_SITES)}, "l2": "flushed before every step (256 MB write)",
                        "parallelism": f"noise sharding x{world}", "matvecs_per_step": wl.matvecs_per_step(),
                        "setup_s": t_setup},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,

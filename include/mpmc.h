@@ -284,31 +284,39 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * the CUDA-core kernel.  Both use the same stored vectors zhat = hi + lo, so
  * the exact correction matches either way.  mpmc_get_option reports whether
  * the tensor-core path is in use (1) or not (0).
- * MPMC_OPT_FAST_STENCIL (default 1): on FP32 / BF16S handles with block
- * widths 16, 32, 64, ..., 1024, the trace-mode and composite stencil steps
- * run the issue-lean kernels: packed FP32x2 arithmetic on (re, im) pairs,
- * links expanded once per field to (re, re, im, im) pairs (16 bytes per
- * link element), compile-time block width, Z4 symbols from a per-block word
- * table (4 bytes per site and right-hand side) and a table-driven noise
- * dot.  Same per-component FMA rounding as the site-parallel kernel; the
- * grouping of the hopping sums differs (FP32 rounding level).
- * MPMC_OPT_FAST_SITES: sites per thread of those kernels (1 .. 16, default
- * 1).  mpmc_get_option(MPMC_OPT_FAST_STENCIL) reports whether they apply to
- * the handle's current block width.
- * MPMC_OPT_SWEEP_STENCIL (default 1): t-sweep form of the stencil steps
- * whose input is a stored block (all but the first step of a noise chain)
- * on handles whose x, y, z extents are even: a CTA walks t over a 2 x 2 x 2
- * block of sites and a tile of right-hand sides, with the block's spinor
- * planes staged in shared memory by TMA, and reads only the three
- * neighbours outside the block from global memory.  1: for the issue-lean
- * kernels (where MPMC_OPT_FAST_STENCIL applies); 2: also for the
- * site-parallel arithmetic on other FP32 / BF16S block widths (with 16-byte
- * rows).  Same arithmetic per site as the non-sweep kernel; only the order
- * of the FP64 per-block dot sums differs.  mpmc_get_option reports 1 or 2
- * where a sweep applies to the handle's current block width, else 0.
+ * Stencil step classes (bits of the two masks below): 1 the dotted steps
+ * (single and projected chains, including the noise-started first step),
+ * 2 the undotted inner steps of composite chains, 4 the outer steps of
+ * composite chains.
+ * MPMC_OPT_FAST_STENCIL (mask 0 .. 7, default 7): classes that run the
+ * issue-lean kernels on FP32 / BF16S handles with block widths 16, 32, 64,
+ * ..., 1024: packed FP32x2 arithmetic on (re, im) pairs, links expanded
+ * once per field to (re, re, im, im) pairs (16 bytes per link element),
+ * compile-time block width, Z4 symbols from a per-block word table (4 bytes
+ * per site and right-hand side) and a table-driven noise dot.  Same
+ * per-component FMA rounding as the site-parallel kernels; the grouping of
+ * the hopping sums differs (FP32 rounding level).  mpmc_get_option returns
+ * the mask in effect for the current block width (0 where they do not
+ * apply).
+ * MPMC_OPT_FAST_SITES: sites per thread of those kernels (1 .. 16, default 1).
+ * MPMC_OPT_SWEEP_STENCIL (mask 0 .. 15, default 7): t-sweep form of the
+ * stencil steps whose input is a stored block, on handles whose x, y, z
+ * extents are even: a CTA walks t over a 2 x 2 x 2 block of sites and a
+ * tile of right-hand sides, with the block's spinor planes staged in shared
+ * memory by TMA, and reads only the three neighbours outside the block from
+ * global memory.  Bits 1, 2, 4: the issue-lean kernels of that class run in
+ * t-sweep form; bit 8: steps outside the issue-lean set (other FP32 / BF16S
+ * block widths with 16-byte rows, or classes not in the fast mask) run the
+ * site-parallel arithmetic in t-sweep form.  Same arithmetic per site as
+ * the non-sweep kernel; only the order of the FP64 per-block dot sums
+ * differs.  mpmc_get_option returns the mask in effect.
  * MPMC_OPT_SWEEP_SEGMENT: t-extent walked by one CTA (0 = automatic, else
  * 1 .. Lt); mpmc_get_option returns the length in effect.  mpmc_autotune
- * sets all four options.
+ * sets all four options: block width and the dotted class's kernel from
+ * noise-started trace chains, then per class the faster of the
+ * site-parallel, issue-lean and t-sweep kernels on chains of that class,
+ * and, when polynomials are set, the fastest of a few class assignments on
+ * one block of the handle's own mpmc_trace_levels.
  */
 enum {
     MPMC_OPT_TENSOR_CORE_DEFLATION = 1,
@@ -336,6 +344,17 @@ MPMC_API int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int fi
  * pointer (same layout); lambda and pair stay on the host.
  */
 MPMC_API int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k);
+
+/*
+ * mpmc_deflation_norms: d_i = z_pair(i)^H gamma5 z_i (k complex values,
+ * interleaved re/im) of the deflation vectors as the handle stores them
+ * (FP64, or the BF16 hi + lo split on reduced-precision handles).  The left
+ * vectors are u_i = gamma5 z_pair(i) / conj(d_i), so that u_i^H z_i = 1
+ * (Secs. 2.2, 4.1); |u_i| = 1 / |d_i| for unit z, and the deflation term of
+ * a level sample grows like 1 / |d_i|, so a caller can drop pairs whose
+ * |d_i| is too small to normalise stably.  Errors: ESTATE (no deflation).
+ */
+MPMC_API int mpmc_deflation_norms(mpmc_handle h, double* d);
 
 /*
  * mpmc_vector_stats: for k device vectors z_i (vector-major, complex double,

@@ -106,9 +106,11 @@ struct mpmc_ctx {
     size_t tc_part_cap = 0;
     int* d_err = nullptr;         // device flag set by kernels whose bounded waits expired
     // t-sweep stencil: option, t-segment length (0 automatic), tensor maps of input buffers
-    int use_sweep = 1;            // 1: t-sweep form of the issue-lean kernels; 2: also the k_sweep kernels
+    // Stencil step classes: bit 0 dotted steps (single / projected chains, incl. the noise-started
+    // first step), bit 1 undotted steps (inner steps of composite chains), bit 2 outer steps.
+    int use_sweep = 7;            // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep
     int sweep_ts = 0;
-    int use_fast = 1;             // issue-lean kernels (FP32 / BF16S, block widths 16 .. 1024)
+    int use_fast = 7;             // issue-lean kernels per class (FP32 / BF16S, block widths 16 .. 1024)
     int fast_sl = 1;              // sites per thread of the issue-lean kernels
     std::vector<SweepMap> maps;
     // work
@@ -199,14 +201,14 @@ void free_ws(Workspace& w) {
 // Launch shape for the workspace's block; grows the accumulators if needed.
 int set_cfg(mpmc_ctx* h, Workspace& w) {
     w.cfg = chain_config(h->g, w.nb, h->tune_bx, h->tune_sl, h->tune_R);
-    w.fast = h->use_fast && fast_supported(w.storage, w.nb);
+    w.fast = (h->use_fast & 7) && fast_supported(w.storage, w.nb);
     if (w.fast) {
         const int per = fast_sites_per_cta(w.nb) * h->fast_sl;
         w.fast_gx = (h->g.V + per - 1) / per;
     }
-    w.fsweep = w.fast && h->use_sweep && fsweep_supported(w.storage, h->g, w.nb);
+    w.fsweep = w.fast && (h->use_sweep & h->use_fast & 7) && fsweep_supported(w.storage, h->g, w.nb);
     if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts);
-    w.sweep = !w.fast && h->use_sweep == 2 && sweep_supported(w.storage, h->g, w.nb);
+    w.sweep = (h->use_sweep & 8) && sweep_supported(w.storage, h->g, w.nb);
     if (w.sweep) w.sw = sweep_config(h->g, w.nb, h->sweep_ts);
     // one accumulator row per site block (k_step) or per site block and t-segment (sweep)
     w.acc_rows = std::max(std::max(w.cfg.gx, w.sweep ? w.sw.rows : 0),
@@ -345,7 +347,8 @@ FastArgs fast_args(const mpmc_ctx* h, const Workspace& ws, double kappa) {
 // for ymode-0 steps of FP32 / BF16S blocks of the compiled widths, else the
 // site-parallel k_step (or k_sweep when selected).
 int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
-    if (ws.fast && a.ymode == 0 && !a.op_only && (a.in || a.dot)) {
+    const int cls = a.dot ? 1 : 2;   // class bit of the step
+    if (ws.fast && (h->use_fast & cls) && a.ymode == 0 && !a.op_only && (a.in || a.dot)) {
         const int kind = a.in ? (a.dot ? 1 : 0) : 2;
         if (kind) if (int rc = ensure_words(h, ws, ns)) return rc;
         FastArgs f = fast_args(h, ws, a.kappa);
@@ -356,7 +359,7 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         f.dot_w[1] = a.dot_w[1];
         f.alpha[0] = (float)a.alpha[0];
         f.alpha[1] = (float)a.alpha[1];
-        const void* fmap = (ws.fsweep && kind < 2) ? sweep_map(h, ws, a.in, 1) : nullptr;
+        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, 1) : nullptr;
         if (fmap) {
             if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep step launch failed");
@@ -387,11 +390,9 @@ int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) 
     return MPMC_OK;
 }
 
-int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
-    const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
-    if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
-    const void* map = ws.sweep ? sweep_map(h, ws, o.in, 0) : nullptr;
-    if (ws.fast) {
+// One outer step (composite chains) on the workspace's launch shape.
+int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
+    if (ws.fast && (h->use_fast & 4)) {
         if (o.dot) if (int rc = ensure_words(h, ws, ns)) return rc;
         FastArgs f = fast_args(h, ws, o.kappa);
         f.in = o.in;
@@ -406,20 +407,30 @@ int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns
             f.beta[i] = (float)o.beta[i];
             f.gamma[i] = (float)o.gamma[i];
         }
-        const void* fmap = ws.fsweep ? sweep_map(h, ws, o.in, 1) : nullptr;
+        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, 1) : nullptr;
         if (fmap) {
             if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep outer launch failed");
         } else if (launch_fast(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fast_gx, h->stream)) {
             return fail(h, MPMC_ECUDA, "issue-lean outer launch failed");
         }
-    } else if (map) {
+        return MPMC_OK;
+    }
+    const void* map = ws.sweep ? sweep_map(h, ws, o.in, 0) : nullptr;
+    if (map) {
         if (launch_sweep_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.sw, map, h->d_err,
                                h->stream))
             return fail(h, MPMC_ECUDA, "t-sweep outer launch failed");
     } else {
         launch_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.cfg, h->stream);
     }
+    return MPMC_OK;
+}
+
+int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
+    const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
+    if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
+    if (int rc = outer_launch(h, ws, o, ns)) return rc;
     if (int rc = prof_end(h)) return rc;
     LAUNCHED(1);
     return MPMC_OK;
@@ -1155,6 +1166,17 @@ static int set_deflation_impl(mpmc_handle h, const double* Z, const double* lamb
     return upload_coefficients(h);
 }
 
+int mpmc_deflation_norms(mpmc_handle h, double* d) {
+    if (!h) return MPMC_EINVAL;
+    if (!d) return fail(h, MPMC_EINVAL, "null output");
+    if (h->k == 0) return fail(h, MPMC_ESTATE, "no deflation vectors set");
+    for (int i = 0; i < h->k; ++i) {
+        d[2 * i] = h->dnorm[i].real();
+        d[2 * i + 1] = h->dnorm[i].imag();
+    }
+    return MPMC_OK;
+}
+
 int mpmc_level_info(mpmc_handle h, int level, double* correction, long long* matvecs) {
     if (!h) return MPMC_EINVAL;
     const int L = num_levels(h);
@@ -1530,28 +1552,40 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     CK(cudaEventCreate(&e1));
     const bool prof = h->prof;
     h->prof = false;
-    double best = INFINITY;
-    int bnb = 0, bR = 1, bbx = 64, bsl = 1, bsweep = 0, bts = 0, bfast = 0, bfsl = 1;
     const int nbs[] = {16, 32, 64, 128, 256, 512, 1024};
     const int bxs[] = {32, 64};
     const int sls[] = {1, 2};
     const NoiseSpec ns{0x5eedULL, 0, 0};
     int rc = MPMC_OK;
-    // time one candidate: a noise-started chain of `steps` fused steps
-    auto trial = [&](int nb) -> int {
+    // time a chain of `steps` launches of one class: 0 dotted (noise-started), 1 undotted, 2 outer
+    auto time_class = [&](int nb, int cls, double* per) -> int {
+        if (rc) return rc;
         if ((rc = ensure_ws(h, h->ws, h->storage, nb))) return rc;
         Workspace& ws = h->ws;
         auto chain = [&]() -> int {
             for (int j = 0; j < steps; ++j) {
-                StepArgs a{};
-                a.in = j == 0 ? nullptr : ws.w[(j - 1) % 2];
-                a.out = ws.w[j % 2];
-                a.dot = true;
-                setc(a.alpha, 0.5);
-                a.kappa = h->kappa;
-                setc(a.dot_w, 1.0);
-                a.acc = ws.acc_hi;
-                if (int r = step_launch(h, ws, a, ns)) return r;
+                if (cls < 2) {
+                    StepArgs a{};
+                    a.in = (cls == 0 && j == 0) ? nullptr : ws.w[j % 2 == 0 ? 1 : 0];
+                    a.out = ws.w[j % 2];
+                    a.dot = cls == 0;
+                    setc(a.alpha, 0.5);
+                    a.kappa = h->kappa;
+                    setc(a.dot_w, 1.0);
+                    a.acc = ws.acc_hi;
+                    if (int r = step_launch(h, ws, a, ns)) return r;
+                } else {
+                    OuterArgs o{};
+                    o.in = ws.w[0];
+                    o.w = ws.w[2 + j % 2];
+                    o.wout = ws.w[3 - j % 2];
+                    o.y = ws.y;
+                    setc(o.alpha, 0.5);
+                    setc(o.beta, 0.25);
+                    setc(o.gamma, 0.125);
+                    o.kappa = h->kappa;
+                    if (int r = outer_launch(h, ws, o, ns)) return r;
+                }
             }
             return cuda_check(h, cudaGetLastError(), "autotune launch");
         };
@@ -1563,77 +1597,142 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
         h->launches += 2 * steps;
-        const double per = ms / ((double)steps * nb * h->g.V);
-        if (per < best) {
-            best = per; bnb = nb; bR = ws.cfg.R; bbx = h->tune_bx; bsl = h->tune_sl;
-            bsweep = ws.fsweep ? 1 : (ws.sweep ? 2 : 0); bts = h->sweep_ts;
-            bfast = ws.fast ? 1 : 0; bfsl = h->fast_sl;
-        }
+        *per = ms / ((double)steps * nb * h->g.V);
         return MPMC_OK;
     };
     const int user_sweep = h->use_sweep, user_fast = h->use_fast;
+    // phase 1: block width and kernel of the dotted steps (the trace-mode chain)
+    double best = INFINITY;
+    int bnb = 0, bR = 1, bbx = 64, bsl = 1, bfast = 0, bsweep = 0, bts = 0, bfsl = 1;
     for (int nb : nbs) {
         if (nb > max_nb) break;
         // the six work vectors of a block must stay within ~24 GB
         if ((size_t)h->g.V * 12 * storage_bytes(h->storage) * 7 * nb > ((size_t)24 << 30)) break;
-        // site-parallel kernel shapes
+        auto consider = [&](double per) {
+            if (per < best) {
+                best = per; bnb = nb; bR = h->ws.cfg.R; bbx = h->tune_bx; bsl = h->tune_sl;
+                bfast = h->use_fast; bfsl = h->fast_sl; bsweep = h->use_sweep; bts = h->sweep_ts;
+            }
+        };
+        double per;
         h->use_sweep = 0;
         h->use_fast = 0;
         for (int R = 1; R <= 2 && !rc; ++R)
             for (int bx : bxs)
                 for (int sl : sls) {
-                    if (rc) break;
                     if (nb / R < bx && bx != bxs[0]) continue;
                     h->tune_R = R; h->tune_bx = bx; h->tune_sl = sl;
-                    trial(nb);
+                    if (time_class(nb, 0, &per)) break;
+                    consider(per);
                 }
-        h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
-        // issue-lean kernels: sites per thread, then their t-sweep form per segment length
-        if (!rc && user_fast && fast_supported(h->storage, nb)) {
+        if (!rc && (user_fast & 1) && fast_supported(h->storage, nb)) {
             h->use_fast = 1;
             for (int fsl : {1, 2, 4}) {
-                if (rc) break;
                 h->fast_sl = fsl;
-                trial(nb);
+                if (time_class(nb, 0, &per)) break;
+                consider(per);
             }
-            if (user_sweep && fsweep_supported(h->storage, h->g, nb)) {
+            if (!rc && (user_sweep & 1) && fsweep_supported(h->storage, h->g, nb)) {
                 h->use_sweep = 1;
-                h->fast_sl = bfast ? bfsl : 1;
                 for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
                     h->sweep_ts = ts;
-                    trial(nb);
+                    if (time_class(nb, 0, &per)) break;
+                    consider(per);
                 }
-                h->use_sweep = 0;
             }
-            h->use_fast = 0;
-        }
-        // k_sweep segment lengths (only when asked for; first step keeps the best site-parallel shape)
-        if (!rc && user_sweep == 2 && !(user_fast && fast_supported(h->storage, nb)) &&
-            sweep_supported(h->storage, h->g, nb)) {
-            h->use_sweep = 2;
+        } else if (!rc && (user_sweep & 8) && sweep_supported(h->storage, h->g, nb)) {
+            h->use_sweep = 8;
+            h->tune_R = 1; h->tune_bx = 32; h->tune_sl = 1;
             for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
                 h->sweep_ts = ts;
-                trial(nb);
+                if (time_class(nb, 0, &per)) break;
+                consider(per);
             }
-            h->use_sweep = 0;
         }
         if (rc) break;
     }
-    h->use_sweep = user_sweep;
-    h->use_fast = user_fast;
+    if (!rc && bnb == 0) rc = fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
+    // phase 2: at that width, the undotted and outer classes choose among the site-parallel
+    // kernel, the issue-lean kernel and its t-sweep form with the parameters found above
+    int fast_mask = bfast & 1, sweep_mask = bsweep & 9;
+    if (!rc) {
+        h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
+        h->fast_sl = bfsl;
+        h->sweep_ts = bts;
+        for (int cls = 1; cls <= 2 && !rc; ++cls) {
+            const int bit = 1 << cls;
+            double bper = INFINITY;
+            int bf = 0, bs = 0;
+            const bool can_fast = (user_fast & bit) && fast_supported(h->storage, bnb);
+            const bool can_sweep = can_fast && (user_sweep & bit) && fsweep_supported(h->storage, h->g, bnb);
+            for (int c = 0; c < 3 && !rc; ++c) {
+                if ((c >= 1 && !can_fast) || (c == 2 && !can_sweep)) continue;
+                h->use_fast = c >= 1 ? bit : 0;
+                h->use_sweep = (c == 2 ? bit : 0) | (bsweep & 8);
+                double per;
+                if (time_class(bnb, cls, &per)) break;
+                if (per < bper) { bper = per; bf = c >= 1; bs = c == 2; }
+            }
+            if (bf) fast_mask |= bit;
+            if (bs) sweep_mask |= bit;
+        }
+    }
     h->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) return rc;
-    if (bnb == 0) return fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
+    if (rc) {
+        h->use_sweep = user_sweep;
+        h->use_fast = user_fast;
+        return rc;
+    }
     h->nb_user = bnb;
     h->tune_R = bR;
     h->tune_bx = bbx;
     h->tune_sl = bsl;
-    h->use_sweep = bsweep;
-    h->sweep_ts = bsweep ? bts : 0;
-    h->use_fast = bfast;
-    h->fast_sl = bfast ? bfsl : 1;
+    h->use_fast = fast_mask;
+    h->fast_sl = bfsl;
+    h->use_sweep = sweep_mask;
+    h->sweep_ts = bts;
+    // phase 3: with polynomials set, time one block of the handle's own multilevel trace for the
+    // class assignment found above and a few alternatives, and keep the fastest
+    const int L = num_levels(h);
+    if (L > 0 && fast_supported(h->storage, bnb) && (user_fast & 7)) {
+        std::vector<double> mean(2 * (size_t)L), var(L);
+        std::vector<std::pair<int, int>> cand = {{fast_mask, sweep_mask}, {0, bsweep & 8}};
+        const bool fsw = fsweep_supported(h->storage, h->g, bnb);
+        for (int fm : {1, 3, 5, 7})
+            for (int sm : {0, 7}) {
+                if (sm && !fsw) continue;
+                const int f = fm & user_fast, sw = (sm & f & user_sweep) | (bsweep & 8);
+                cand.emplace_back(f, sw);
+            }
+        double tbest = INFINITY;
+        std::pair<int, int> best_c = cand[0];
+        const bool prof3 = h->prof;
+        h->prof = false;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        int rc3 = MPMC_OK;
+        for (size_t c = 0; c < cand.size() && !rc3; ++c) {
+            h->use_fast = cand[c].first;
+            h->use_sweep = cand[c].second;
+            if (c == 0) rc3 = mpmc_trace_levels(h, 0x5eedULL, bnb, 0, mean.data(), var.data(), nullptr);   // warm-up
+            if (rc3) break;
+            cudaEventRecord(e0, h->stream);
+            rc3 = mpmc_trace_levels(h, 0x5eedULL, bnb, 0, mean.data(), var.data(), nullptr);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc3 && ms < tbest) { tbest = ms; best_c = cand[c]; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->prof = prof3;
+        h->use_fast = best_c.first;
+        h->use_sweep = best_c.second;
+        if (rc3) return rc3;
+    }
     return ensure_ws(h, h->ws, h->storage, bnb);
 }
 
@@ -1644,7 +1743,7 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->use_tc = value != 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            if (value < 0 || value > 2) return fail(h, MPMC_EINVAL, "sweep option is 0, 1 or 2");
+            if (value < 0 || value > 15) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 15");
             h->use_sweep = value;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
@@ -1652,7 +1751,8 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->sweep_ts = value;
             return MPMC_OK;
         case MPMC_OPT_FAST_STENCIL:
-            h->use_fast = value != 0;
+            if (value < 0 || value > 7) return fail(h, MPMC_EINVAL, "fast-stencil option is a mask in 0 .. 7");
+            h->use_fast = value;
             return MPMC_OK;
         case MPMC_OPT_FAST_SITES:
             if (value < 1 || value > 16) return fail(h, MPMC_EINVAL, "sites per thread out of range");
@@ -1673,19 +1773,21 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
         case MPMC_OPT_TENSOR_CORE_DEFLATION:
             *value = (h->use_tc && h->tc_ready && h->storage != ST_F64) ? 1 : 0;
             return MPMC_OK;
-        case MPMC_OPT_SWEEP_STENCIL:
-            if (h->use_fast && fast_supported(h->storage, cur_nb(h)))
-                *value = (h->use_sweep && fsweep_supported(h->storage, h->g, cur_nb(h))) ? 1 : 0;
-            else
-                *value = (h->use_sweep == 2 && sweep_supported(h->storage, h->g, cur_nb(h))) ? 2 : 0;
+        case MPMC_OPT_SWEEP_STENCIL: {
+            int v = 0;
+            if (fast_supported(h->storage, cur_nb(h)) && fsweep_supported(h->storage, h->g, cur_nb(h)))
+                v |= h->use_sweep & h->use_fast & 7;
+            if (sweep_supported(h->storage, h->g, cur_nb(h))) v |= h->use_sweep & 8;
+            *value = v;
             return MPMC_OK;
+        }
         case MPMC_OPT_SWEEP_SEGMENT:
-            *value = (h->use_fast && fsweep_supported(h->storage, h->g, cur_nb(h)))
+            *value = ((h->use_fast & 7) && fsweep_supported(h->storage, h->g, cur_nb(h)))
                          ? fsweep_config(h->g, cur_nb(h), h->sweep_ts).ts
                          : sweep_config(h->g, cur_nb(h), h->sweep_ts).ts;
             return MPMC_OK;
         case MPMC_OPT_FAST_STENCIL:
-            *value = (h->use_fast && fast_supported(h->storage, cur_nb(h))) ? 1 : 0;
+            *value = fast_supported(h->storage, cur_nb(h)) ? (h->use_fast & 7) : 0;
             return MPMC_OK;
         case MPMC_OPT_FAST_SITES:
             *value = h->fast_sl;

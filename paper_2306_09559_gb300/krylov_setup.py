@@ -24,6 +24,9 @@ from . import mpmc as G
 
 IMAGLIM = 2e-4
 EVECTOL = 1e-3
+# Smallest |d_i| = |z_pair(i)^H gamma5 z_i| (unit z) kept: the normalised left
+# vector has norm 1/|d_i| and the deflation term of a sample grows with it.
+DNORM_MIN = 1e-2
 
 
 def harmonic_ritz(hbar, m):
@@ -147,6 +150,19 @@ class Setup:
         keep, pair = self.select(lam, stats, imaglim, evectol, kmax)
         Zsel = Zd[torch.as_tensor(keep, device=Zd.device)].contiguous() if keep.size else Zd[:0]
         return Zsel, lam[keep], pair
+
+    @staticmethod
+    def well_conditioned(d, pair, dmin=DNORM_MIN):
+        """Indices of the pairs to keep: |d_i| >= dmin for i and its partner.
+
+        Returns (keep, new pair map of the kept list).
+        """
+        ok = np.abs(d) >= dmin
+        ok &= ok[pair]                      # a conjugate pair stays or goes together
+        keep = np.flatnonzero(ok)
+        pos = -np.ones(len(d), dtype=np.int64)
+        pos[keep] = np.arange(keep.size)
+        return keep, pos[pair[keep]].astype(np.int32)
 
     def projected_start(self, seed):
         """A Z4 vector after one Left-right Projection, normalised (Sec. 5, step 2c).

@@ -67,6 +67,7 @@ _SIGS = {
     "mpmc_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mpmc_set_deflation_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int]),
+    "mpmc_deflation_norms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "mpmc_deflation_dots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -138,6 +139,7 @@ class Handle:
         self.dims = (lx, ly, lz, lt)
         self.V = lx * ly * lz * lt
         self.n = 12 * self.V
+        self.k = 0
         self.precision = precision
         self.kappa = kappa
         dims = (ctypes.c_int * 4)(lx, ly, lz, lt)
@@ -218,6 +220,7 @@ class Handle:
         lam = _c128(lam) if k else None
         pr = np.ascontiguousarray(pair, dtype=np.int32) if k else None
         self._check(self._L.mpmc_set_deflation(self._h, _ptr(Zt), _ptr(lam), _ptr(pr), k), "mpmc_set_deflation")
+        self.k = k
 
     # ----------------------------------------------------------------- compute
     def _block_call(self, fn, what, X, *pre):
@@ -300,12 +303,20 @@ class Handle:
         self._check(self._L.mpmc_get_option(self._h, int(option), ctypes.byref(v)), "mpmc_get_option")
         return v.value
 
+    def mpmc_deflation_norms(self):
+        """d_i = z_pair(i)^H gamma5 z_i of the stored deflation vectors (complex, length k)."""
+        k = self.k
+        d = np.zeros(k, dtype=np.complex128)
+        self._check(self._L.mpmc_deflation_norms(self._h, _ptr(d)), "mpmc_deflation_norms")
+        return d
+
     def mpmc_set_deflation_device(self, Zd, lam, pair):
         """Zd: CUDA complex128 tensor (k, n), row i = z_i."""
         lam = _c128(lam)
         pr = np.ascontiguousarray(pair, dtype=np.int32)
         self._check(self._L.mpmc_set_deflation_device(self._h, _ptr(Zd), _ptr(lam), _ptr(pr), int(Zd.shape[0])),
                     "mpmc_set_deflation_device")
+        self.k = int(Zd.shape[0])
 
     def mpmc_vector_stats(self, Zd):
         """Zd: CUDA complex128 tensor (k, n); returns (k, 4) float64 stats."""

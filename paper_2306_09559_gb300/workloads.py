@@ -123,11 +123,20 @@ def setup(h64, wl, log=None):
     defl = None
     if wl.k > 0:
         Zd, lam, pair = S.eigenpairs(pin, v0, wl.arnoldi_m, wl.ndefinit, kmax=wl.k)
-        if log:
-            log(f"setup: {lam.size} of {wl.ndefinit} Ritz pairs accepted (want {wl.k}); "
-                f"|lambda| in [{np.abs(lam).min():.4g}, {np.abs(lam).max():.4g}]")
-        defl = (Zd, lam, pair)
         h64.mpmc_set_deflation_device(Zd, lam, pair)
+        # pairs whose left vector cannot be normalised stably (|d_i| small) are dropped
+        d = h64.mpmc_deflation_norms()
+        keep, pair2 = krylov_setup.Setup.well_conditioned(d, np.asarray(pair))
+        if log:
+            log(f"setup: {lam.size} of {wl.ndefinit} Ritz pairs accepted (want {wl.k}), "
+                f"{keep.size} with |d_i| >= {krylov_setup.DNORM_MIN} (min |d_i| {np.abs(d).min():.3g}); "
+                f"|lambda| in [{np.abs(lam).min():.4g}, {np.abs(lam).max():.4g}]")
+        if keep.size < lam.size:
+            import torch
+            Zd = Zd[torch.as_tensor(keep, device=Zd.device)].contiguous()
+            lam, pair = lam[keep], pair2
+            h64.mpmc_set_deflation_device(Zd, lam, pair)
+        defl = (Zd, lam, pair)
     polys = []
     for lv in wl.levels:
         if lv[0] == "single":

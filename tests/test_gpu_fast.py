@@ -97,9 +97,9 @@ CASES = [((4, 4, 4, 4), 1, 16), ((4, 4, 4, 4), 1, 32), ((3, 5, 2, 3), -1, 16), (
 def test_fast_matches_site_parallel_and_oracle(dims, bc_t, block, prec, sl):
     setup = _setup(dims, bc_t)
     N = block + block // 2          # two blocks, the second one ragged
-    on, used = _trace(dims, bc_t, prec, block, 1, sl, N, setup=setup)
+    on, used = _trace(dims, bc_t, prec, block, 7, sl, N, setup=setup)
     off, used0 = _trace(dims, bc_t, prec, block, 0, sl, N, setup=setup)
-    assert used[0] == 1 and used0[0] == 0
+    assert used[0] == 7 and used0[0] == 0
     _check(setup, on, off, prec, N, 2e-6 if prec == G.FP32 else 2e-3)
 
 
@@ -114,9 +114,9 @@ def test_fast_sweep_matches_fast_and_oracle(dims, bc_t, block, prec, segment):
         pytest.skip("segment longer than the lattice")
     setup = _setup(dims, bc_t)
     N = block + block // 2
-    sw, used = _trace(dims, bc_t, prec, block, 1, 1, N, setup=setup, sweep=1, segment=segment)
-    plain, used0 = _trace(dims, bc_t, prec, block, 1, 1, N, setup=setup, sweep=0)
-    assert used[:2] == (1, 1) and used0[:2] == (1, 0)
+    sw, used = _trace(dims, bc_t, prec, block, 7, 1, N, setup=setup, sweep=7, segment=segment)
+    plain, used0 = _trace(dims, bc_t, prec, block, 7, 1, N, setup=setup, sweep=0)
+    assert used[:2] == (7, 7) and used0[:2] == (7, 0)
     assert 1 <= used[2] <= dims[3] and (segment == 0 or used[2] == segment)
     _check(setup, sw, plain, prec, N, 2e-6 if prec == G.FP32 else 2e-3)
 
@@ -126,9 +126,9 @@ def test_fast_sweep_matches_fast_and_oracle(dims, bc_t, block, prec, segment):
 def test_fast_wide_blocks(block, sweep):
     dims = (4, 4, 2, 4)
     setup = _setup(dims, 1)
-    on, used = _trace(dims, 1, G.FP32, block, 1, 1, block, setup=setup, defl=False, sweep=sweep)
+    on, used = _trace(dims, 1, G.FP32, block, 7, 1, block, setup=setup, defl=False, sweep=7 * sweep)
     off, _ = _trace(dims, 1, G.FP32, block, 0, 1, block, setup=setup, defl=False)
-    assert used[:2] == (1, sweep)
+    assert used[:2] == (7, 7 * sweep)
     n = 12 * int(np.prod(dims))
     for level in range(3):
         scale = n + np.max(np.abs(off[level]))
@@ -137,14 +137,30 @@ def test_fast_wide_blocks(block, sweep):
 
 def test_fast_not_used_where_it_does_not_apply():
     setup = _setup((4, 4, 4, 4), 1)
-    _, used = _trace((4, 4, 4, 4), 1, G.FP32, 24, 1, 1, 24, setup=setup)
+    _, used = _trace((4, 4, 4, 4), 1, G.FP32, 24, 7, 1, 24, setup=setup)
     assert used[0] == 0                  # block width outside the compiled set
-    _, used = _trace((4, 4, 4, 4), 1, G.FP64, 32, 1, 1, 32, setup=setup)
+    _, used = _trace((4, 4, 4, 4), 1, G.FP64, 32, 7, 1, 32, setup=setup)
     assert used[0] == 0                  # FP64 keeps the site-parallel kernel
+
+
+@pytest.mark.parametrize("mask", [1, 2, 4, 5])
+def test_fast_per_class_masks(mask):
+    """Any subset of step classes (dotted, undotted inner, outer) on the issue-lean
+    kernels, the rest on the site-parallel ones, gives the same samples."""
+    dims = (4, 4, 4, 4)
+    setup = _setup(dims, 1)
+    N = 48
+    part, used = _trace(dims, 1, G.FP32, 32, mask, 1, N, setup=setup, sweep=mask)
+    off, _ = _trace(dims, 1, G.FP32, 32, 0, 1, N, setup=setup)
+    assert used[:2] == (mask, mask)
+    _check(setup, part, off, G.FP32, N, 2e-6)
 
 
 def test_fast_sites_option_range():
     with G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, G.FP32, 1) as h:
+        for bad in (-1, 8):
+            with pytest.raises(G.MpmcError):
+                h.mpmc_set_option(G.OPT_FAST_STENCIL, bad)
         for bad in (0, 17):
             with pytest.raises(G.MpmcError) as e:
                 h.mpmc_set_option(G.OPT_FAST_SITES, bad)

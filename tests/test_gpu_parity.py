@@ -478,3 +478,13 @@ def test_error_codes():
         with pytest.raises(G.MpmcError) as e:
             h.mpmc_set_block(5000)
         assert e.value.code == G.MPMC_EINVAL
+
+
+def test_deflation_norms_match_oracle():
+    """d_i = z_pair(i)^H gamma5 z_i as stored (FP64 handle) against the oracle's normalisation."""
+    op, polys, lam, Z, pair = small_setup()
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        d = h.mpmc_deflation_norms()
+    ref = np.einsum('ni,ni->i', op.gamma5(Z[:, pair]).conj(), Z)
+    assert np.max(np.abs(d - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))

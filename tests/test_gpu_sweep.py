@@ -1,6 +1,7 @@
 """The k_sweep stencil kernels (TMA-staged planes of a 2 x 2 x 2 site block,
 site-parallel arithmetic).  The issue-lean kernels are switched off here and
-the sweep option set to 2, so that every step with a memory input runs
+the sweep option set to 8 (k_sweep for every step outside the issue-lean
+set), so that every step with a memory input runs
 k_sweep / its outer form.
 
 Each case runs the same call with the sweep kernels on and off (the
@@ -37,7 +38,7 @@ def _apply_op(dims, bc_t, prec, nrhs, sweep, segment=0, block=0):
         if block:
             h.mpmc_set_block(block)
         h.mpmc_set_option(G.OPT_FAST_STENCIL, 0)
-        h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 2 * sweep)
+        h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 8 * sweep)
         h.mpmc_set_option(G.OPT_SWEEP_SEGMENT, segment)
         X = synth.random_block(12 * int(np.prod(dims)), nrhs, 8)
         Y = h.mpmc_apply_op(X)
@@ -55,7 +56,7 @@ def test_sweep_apply_op(dims, bc_t, prec, nrhs, segment):
     op = operator(dims, "near_identity", 3, 0.124, 0.3, bc_t)
     X, Y1, used, seg = _apply_op(dims, bc_t, prec, nrhs, 1, segment)
     _, Y0, used0, _ = _apply_op(dims, bc_t, prec, nrhs, 0, segment)
-    assert used == 2 and used0 == 0
+    assert used == 8 and used0 == 0
     assert seg == (segment if segment else seg) and 1 <= seg <= dims[3]
     ref = op(X)
     scale = np.max(np.abs(ref))
@@ -76,7 +77,7 @@ def test_sweep_not_used_where_it_does_not_apply():
 def test_sweep_segment_range():
     with G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, G.FP32, 1) as h:
         with pytest.raises(G.MpmcError):
-            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 3)
+            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 16)
         with pytest.raises(G.MpmcError) as e:
             h.mpmc_set_option(G.OPT_SWEEP_SEGMENT, 5)
         assert e.value.code == G.MPMC_EINVAL
@@ -104,12 +105,12 @@ def test_sweep_trace_levels(prec, block, segment):
         with G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, prec, 1) as h:
             h.mpmc_set_block(block)
             h.mpmc_set_option(G.OPT_FAST_STENCIL, 0)
-            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 2 * sweep)
+            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 8 * sweep)
             h.mpmc_set_option(G.OPT_SWEEP_SEGMENT, segment)
             h.mpmc_set_deflation(Z, lam, pair)
             set_polys(h, polys)
             out[sweep] = h.mpmc_trace_levels(seed=77, nsamples=N)[2]
-            assert h.mpmc_get_option(G.OPT_SWEEP_STENCIL) == 2 * sweep
+            assert h.mpmc_get_option(G.OPT_SWEEP_STENCIL) == 8 * sweep
     for level in range(3):
         ref, hi, lo, dt = M.level_sample_parts(op, polys, level, 77, N, defl)
         mag = np.abs(hi) + np.abs(lo) + np.abs(dt)
@@ -130,12 +131,12 @@ def test_autotune_sets_sweep_options():
     with G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, G.FP32, 1) as h:
         h.mpmc_set_deflation(Z, lam, pair)
         set_polys(h, polys)
-        h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 2)
+        h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 15)
         cfg = h.mpmc_autotune(64)
         used = h.mpmc_get_option(G.OPT_SWEEP_STENCIL)
         fast = h.mpmc_get_option(G.OPT_FAST_STENCIL)
         seg = h.mpmc_get_option(G.OPT_SWEEP_SEGMENT)
-        assert used in (0, 1, 2) and fast in (0, 1) and not (used == 2 and fast) and 1 <= seg <= 4
+        assert 0 <= used <= 15 and 0 <= fast <= 7 and (used & 7 & ~fast) == 0 and 1 <= seg <= 4
         s = h.mpmc_trace_levels(seed=5, nsamples=20)[2]
     ref = M.level_samples(op, polys, 2, 5, 20)
     assert np.max(np.abs(s[2] - ref)) < 1e-5 * op.n
