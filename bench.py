@@ -28,6 +28,10 @@ if ROOT not in sys.path:
 
 METRIC = "noise-vector poly applies/s, dslash HBM GB/s; mixed vs FP64 at equal trace err"
 UNIT = "noise-vector poly applies/s"
+BATCH_KEY = "batch64"
+BATCH_DESC = ("64 independent Wilson-Dirac instances, lattices from {4^4, 6^4, 8^4, 8^3x16, 12^4}, "
+              "kappa ~ U[0.118, 0.124], near-identity links eps ~ U[0.2, 0.4]; levels [composite20x15=deg299, "
+              "deg40, deg8] each; 32 Z4 noises/level; one CUDA graph per batch")
 FLOPS_PER_SITE_RHS_STEP = 1488   # 1320 hopping + 48 diagonal + 96 chain axpy + 24 Z4 dot
 
 
@@ -102,6 +106,26 @@ def oracle_worker(spec):
     from oracle.lattice import WilsonOperator
     from paper_2306_09559_gb300 import workloads, synth
 
+    if spec["workload"] == BATCH_KEY:
+        # one noise vector through a degree-8 polynomial on each lattice class of the batch;
+        # the step's cost is extrapolated by the matvecs of every instance on its class
+        from oracle import philox
+        from oracle import polynomial as P
+        insts = workloads.batch_instances()
+        per_class = {}
+        for dims in sorted(set(w.dims for w in insts)):
+            wl0 = next(w for w in insts if w.dims == dims)
+            op = WilsonOperator(workloads.gauge(wl0), wl0.kappa)
+            b = philox.z4_block(wl0.noise_seed, 0, 0, 1, wl0.V)
+            roots = np.linspace(1.0, 2.0, 9) + 0.1j
+            t1 = time.perf_counter()
+            np.vdot(b[:, 0], P.apply_poly(op, roots, b)[:, 0])
+            per_class[dims] = (time.perf_counter() - t1) / 8
+        t_step = sum(per_class[w.dims] * w.matvecs_per_step() for w in insts)
+        return {"times": [t_step] * spec["steps"], "applies_per_step": sum(w.applies_per_step() for w in insts),
+                "setup_s": 0.0,
+                "sample": "1 noise vector through a degree-8 polynomial on each of the 5 lattice classes, "
+                          f"extrapolated by the batch's {sum(w.matvecs_per_step() for w in insts)} matvecs"}
     wl = workloads.get(spec["workload"])
     per_level = spec["per_level"]
     U = workloads.gauge(wl)
@@ -197,7 +221,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     from paper_2306_09559_gb300 import workloads
-    wl = workloads.get(args.workload)
+    wl = workloads.get(args.workload) if args.workload != BATCH_KEY else None
     per_level = args.oracle_noises
     res = run_oracle(args.workload, per_level, args.steps + args.warmup)
     times = res["times"][args.warmup:]
@@ -206,12 +230,190 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.describe(), "sample": res["sample"]},
+        "config": {"workload": wl.describe() if wl else BATCH_DESC, "sample": res["sample"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{res['sample']} (FP64 numpy oracle, 1 thread, {cpu_model()})"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ batched instances
+def batch_arm(args):
+    """The uneven batch: 64 instances as one captured CUDA graph per step (mixed
+    precision), against the same handles traced one after another and the FP64
+    batch.  Weak scaling: rank r runs its own 64 instances (noise offset r)."""
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    oracle_proc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        tmp = tempfile.NamedTemporaryFile("r", suffix=".json", delete=False)
+        tmp.close()
+        spec = json.dumps({"workload": BATCH_KEY, "per_level": 1, "steps": 1, "out": tmp.name})
+        oracle_proc = (subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                                        env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True),
+                       tmp.name)
+
+    from paper_2306_09559_gb300 import build, workloads
+    from paper_2306_09559_gb300 import mpmc as G
+    build.build()
+    insts = workloads.batch_instances()
+    prec = {"fp32": G.FP32, "bf16s": G.BF16S, "fp64": G.FP64}[args.precision]
+    t0 = time.perf_counter()
+    links, h64s, hms = [], [], []
+    for wl in insts:
+        U = workloads.gauge(wl)
+        links.append(np.ascontiguousarray(U))
+        h64 = G.Handle(U, wl.kappa, G.FP64)
+        polys = workloads.setup_light(h64, wl)
+        workloads.configure(h64, polys, None, wl.nsamples)
+        hm = G.Handle(U, wl.kappa, prec)
+        workloads.configure(hm, polys, None, wl.nsamples)
+        h64s.append(h64)
+        hms.append(hm)
+    t_setup = time.perf_counter() - t0
+    first = rank * 32
+    applies = sum(w.applies_per_step() for w in insts)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    cur = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        """device time per step (events on the current stream, synchronised on both sides)."""
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(cur)
+            res = fn()
+            e1.record(cur)
+            torch.cuda.synchronize()
+            out.append((e0.elapsed_time(e1), res))
+        return out
+
+    bm = G.Batch(hms)
+    run_batch = lambda: bm.mpmc_batch_trace_levels(7, 32, first)
+    for _ in range(args.warmup):
+        run_batch()
+    n0 = bm.mpmc_batch_launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.nvtx.range_push("timed")
+        res = timed(run_batch, args.steps)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+    launches = bm.mpmc_batch_launch_count() - n0
+    t_local = sum(t for t, _ in res)
+    t_max = t_local
+    if dist is not None:
+        tt = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = applies * world / (ms_per_step / 1000.0)
+    mean_m, var_m = res[-1][1]
+
+    # the same handles traced one after another (no graph)
+    seq = timed(lambda: [h.mpmc_trace_levels(7, 32, first, want_samples=False) for h in hms], 2)
+    seq_ms = sum(t for t, _ in seq) / len(seq)
+    # FP64 batch
+    b64 = G.Batch(h64s)
+    b64.mpmc_batch_trace_levels(7, 32, first)
+    r64 = timed(lambda: b64.mpmc_batch_trace_levels(7, 32, first), 1)
+    t64 = r64[0][0]
+    mean64, var64 = r64[0][1]
+    L = 3
+    var_sum64, var_sum_m = float(np.sum(var64[:, :L])), float(np.sum(var_m[:, :L]))
+    # the paired comparison per level, pooled over instances (same noise on both)
+    z = [float(np.max(np.abs((mean_m[:, l] - mean64[:, l]).real) / np.sqrt(var64[:, l] / 32))) for l in range(L)]
+    fp64 = {"value": applies / (t64 / 1000.0), "ms_per_step": t64,
+            "equal_se_speedup": (t64 * var_sum64) / (ms_per_step * var_sum_m),
+            "max_over_instances_mean_diff_over_se": z}
+
+    # end to end through the public API: new links for every instance (host -> device), the
+    # batch (recaptured, since the fields changed), means and variances back to the host
+    pinned = [torch.from_numpy(u).pin_memory() for u in links]
+    h2d = sum(int(p.numel() * p.element_size()) for p in pinned)
+
+    def e2e_step():
+        for h, p in zip(hms, pinned):
+            h.mpmc_set_links(p)
+        return bm.mpmc_batch_trace_levels(7, 32, first)
+
+    e2e_res = timed(e2e_step, 2)
+    e2e_ms = sum(t for t, _ in e2e_res) / len(e2e_res)
+    e2e = {"value": applies / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": len(insts) * 8 * 24, "ms_per_step": e2e_ms,
+           "note": "host links copied to every handle each step, so the graph is captured again each step"}
+
+    # throughput of the stencil steps of a batch step: algorithmic bytes of all steps / step time
+    stor = {"fp32": 8, "bf16s": 4, "fp64": 16}[args.precision]
+    lb = 72 if args.precision != "fp64" else 144
+    alg = 0.0
+    for w in insts:
+        per_step = w.V * w.nsamples * 12 * stor * 2 + w.V * 4 * lb
+        alg += per_step * w.matvecs_per_step() / w.nsamples
+    hbm, sm_max, src = peaks()
+    achieved = alg / (ms_per_step / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "all stencil steps of the batch (one graph)",
+                "hbm_peak_source": src, "algorithmic_bytes_per_step": alg,
+                "note": "step-level: every launch of the 64 instances counted, timed as one graph; the working "
+                        "set of most instances is L2-resident"}
+    cpu = None
+    if oracle_proc is not None:
+        proc, path = oracle_proc
+        _, err = proc.communicate()
+        if proc.returncode == 0:
+            r = json.load(open(path))
+            cpu = {"value": r["applies_per_step"] / r["times"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{r['sample']}; FP64 numpy oracle, 1 thread, {cpu_model()}"}
+        else:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
+        os.unlink(path)
+    if rank == 0:
+        lat = {}
+        for w in insts:
+            lat["x".join(map(str, w.dims))] = lat.get("x".join(map(str, w.dims)), 0) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16s": "bf16-stored/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": BATCH_DESC, "instances": len(insts), "lattices": lat,
+                       "noises_per_level": 32, "applies_per_step": applies,
+                       "matvecs_per_step": sum(w.matvecs_per_step() for w in insts),
+                       "graph_nodes_per_step": launches // max(args.steps, 1),
+                       "sequential_ms_per_step": seq_ms, "graph_speedup_over_sequential": seq_ms / ms_per_step,
+                       "l2": "flushed before every step (256 MB write)", "parallelism": f"instances x{world}",
+                       "setup_s": t_setup},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu, "fp64": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    bm.close()
+    b64.close()
+    for h in hms + h64s:
+        h.close()
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -461,6 +663,8 @@ def main():
         return reference_arm(args)
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")
+    if args.workload == BATCH_KEY:
+        return batch_arm(args)
     return gpu_arm(args)
 
 

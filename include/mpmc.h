@@ -375,6 +375,35 @@ MPMC_API int mpmc_vector_stats(mpmc_handle h, const double* Z, int k, double* st
 MPMC_API int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, int on_device);
 
 /*
+ * Batches of independent instances (lattices of uneven size, their own kappa,
+ * polynomials, deflation and precision): the multilevel estimates of all
+ * handles in a batch run as parallel branches of one captured CUDA graph, so
+ * that small instances overlap on the GPU and the batch costs one graph
+ * launch on the host.  The paper treats one lattice at a time; this is the
+ * batched form of mpmc_trace_levels for many of them.
+ *
+ * mpmc_batch_create: handles are borrowed (the caller keeps and destroys
+ * them, after the batch); each must be on its own stream (not the legacy
+ * default stream).  mpmc_batch_trace_levels: noise vectors first ..
+ * first+nsamples-1 of every handle (each with its own noise seed `seed`
+ * and level ids as in mpmc_trace_levels); mean[2*(i*MPMC_MAX_POLYS + l)]
+ * (complex) and var[i*MPMC_MAX_POLYS + l] receive level l of handle i (as
+ * mpmc_trace_levels would return them, bit for bit).  The graph is captured
+ * on the first call (after one plain run, which does any lazy allocation)
+ * and replayed while (seed, nsamples, first) and every handle's state stay
+ * the same; changing a handle (polynomials, deflation, links, options,
+ * block, stream, autotune) recaptures it.  mpmc_batch_launch_count: kernel
+ * nodes replayed so far.  Errors: as mpmc_trace_levels, EINVAL (a handle on
+ * the legacy default stream), ECUDA (capture or launch failed).
+ */
+typedef struct mpmc_batch* mpmc_batch_handle;
+MPMC_API int mpmc_batch_create(mpmc_batch_handle* b, int n, const mpmc_handle* handles);
+MPMC_API int mpmc_batch_trace_levels(mpmc_batch_handle b, uint64_t seed, int nsamples, int first, double* mean,
+                                     double* var);
+MPMC_API long long mpmc_batch_launch_count(mpmc_batch_handle b);
+MPMC_API int mpmc_batch_destroy(mpmc_batch_handle b);
+
+/*
  * mpmc_trace_poly_noalloc: Hutchinson samples s_j = b_j^H p(A) b_j of one
  * polynomial, j = first .. first+nsamples-1 (Z4 noise of level id `level`,
  * same bits as mpmc_noise), computed without allocating any device memory.

@@ -126,6 +126,7 @@ struct mpmc_ctx {
     double* kr_nrm = nullptr;
     int kr_m = 0;
     long long launches = 0;
+    unsigned long long gen = 0;   // bumped by every call that changes what a trace launches
     // profiling: events around kernel launches of each class (mpmc_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -1042,6 +1043,7 @@ int mpmc_destroy(mpmc_handle h) {
 }
 
 int mpmc_set_stream(mpmc_handle h, void* stream) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     CK(cudaStreamSynchronize(h->stream));
     h->stream = stream ? (cudaStream_t)stream : h->own;
@@ -1049,6 +1051,7 @@ int mpmc_set_stream(mpmc_handle h, void* stream) {
 }
 
 int mpmc_set_block(mpmc_handle h, int nb) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     if (nb < 0 || nb > MPMC_MAX_BLOCK) return fail(h, MPMC_EINVAL, "block size out of range");
     h->nb_user = nb;
@@ -1057,6 +1060,7 @@ int mpmc_set_block(mpmc_handle h, int nb) {
 
 int mpmc_set_poly(mpmc_handle h, int index, int kind, const double* roots, int nroots, const double* outer,
                   int nouter, int leja) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
     if (kind != MPMC_SINGLE && kind != MPMC_COMPOSITE && kind != MPMC_DEFLATED_COMPOSITE)
@@ -1295,8 +1299,11 @@ int mpmc_noise(mpmc_handle h, uint64_t seed, int level, int first, int nrhs, dou
     return MPMC_OK;
 }
 
-int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, double* mean, double* var,
-                      double* samples) {
+// mpmc_trace_levels in three stages, so that a batch of handles can capture the
+// launches of many traces in one CUDA graph: checks and every allocation; the
+// kernel launches on h->stream (no allocation, no host synchronisation); the
+// copy of the samples to the host and the statistics.
+int trace_prepare(mpmc_ctx* h, int nsamples, int first, int* nb_out) {
     if (!h) return MPMC_EINVAL;
     if (nsamples < 1 || first < 0) return fail(h, MPMC_EINVAL, "nsamples must be >= 1 and first >= 0");
     const int L = num_levels(h);
@@ -1311,9 +1318,15 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
         if (int rc = dev_alloc(h, &h->samples, sizeof(double2) * need)) return rc;
         h->samples_cap = need;
     }
-    Workspace& ws = h->ws;
     if (h->polys[0].kind == MPMC_DEFLATED_COMPOSITE)
         if (int rc = ensure_projection(h)) return rc;
+    *nb_out = nb;
+    return MPMC_OK;
+}
+
+int trace_enqueue(mpmc_ctx* h, uint64_t seed, int nsamples, int first, int nb) {
+    const int L = num_levels(h);
+    Workspace& ws = h->ws;
     for (int l = 0; l < L; ++l) {
         const bool has_lo = l + 1 < L;
         const bool proj = h->polys[l].kind == MPMC_DEFLATED_COMPOSITE;
@@ -1351,6 +1364,12 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
             LAUNCHED(1);
         }
     }
+    return MPMC_OK;
+}
+
+int trace_collect(mpmc_ctx* h, int nsamples, double* mean, double* var, double* samples) {
+    const int L = num_levels(h);
+    const size_t need = (size_t)L * nsamples;
     std::vector<double2> hs(need);
     CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1381,6 +1400,15 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
             }
     }
     return MPMC_OK;
+}
+
+int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, double* mean, double* var,
+                      double* samples) {
+    if (!h) return MPMC_EINVAL;
+    int nb = 0;
+    if (int rc = trace_prepare(h, nsamples, first, &nb)) return rc;
+    if (int rc = trace_enqueue(h, seed, nsamples, first, nb)) return rc;
+    return trace_collect(h, nsamples, mean, var, samples);
 }
 
 int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m, double* hbar, double* basis, int* steps) {
@@ -1507,6 +1535,7 @@ int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* launches, d
 }
 
 int mpmc_set_links(mpmc_handle h, const double* links) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     if (!links) return fail(h, MPMC_EINVAL, "null links");
     const size_t nl = (size_t)h->g.V * 36;
@@ -1525,6 +1554,7 @@ int mpmc_set_links(mpmc_handle h, const double* links) {
 }
 
 int mpmc_set_launch(mpmc_handle h, int R, int bx, int sl) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     if (R < 0 || R > 2 || bx < 0 || bx > 256 || (bx & (bx - 1)) || sl < 0 || sl > 16)
         return fail(h, MPMC_EINVAL, "launch shape out of range");
@@ -1544,6 +1574,7 @@ int mpmc_get_launch(mpmc_handle h, int* nb, int* R, int* bx, int* sl) {
 }
 
 int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     if (max_nb < 1 || max_nb > MPMC_MAX_BLOCK) return fail(h, MPMC_EINVAL, "max_nb out of range");
     if (steps < 1) steps = 6;
@@ -1698,24 +1729,32 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     const int L = num_levels(h);
     if (L > 0 && fast_supported(h->storage, bnb) && (user_fast & 7)) {
         std::vector<double> mean(2 * (size_t)L), var(L);
-        std::vector<std::pair<int, int>> cand = {{fast_mask, sweep_mask}, {0, bsweep & 8}};
+        // (fast mask, sweep mask, site-parallel shape R, bx, sl)
+        struct Cand { int f, sw, R, bx, sl; };
+        std::vector<Cand> cand = {{fast_mask, sweep_mask, bR, bbx, bsl}};
         const bool fsw = fsweep_supported(h->storage, h->g, bnb);
-        for (int fm : {1, 3, 5, 7})
-            for (int sm : {0, 7}) {
-                if (sm && !fsw) continue;
-                const int f = fm & user_fast, sw = (sm & f & user_sweep) | (bsweep & 8);
-                cand.emplace_back(f, sw);
-            }
+        const int shapes[][3] = {{bR, bbx, bsl}, {1, 32, 2}, {1, 64, 1}, {2, 32, 1}};
+        for (const auto& sh : shapes)
+            for (int fm : {0, 1, 3, 5, 7})
+                for (int sm : {0, 7}) {
+                    if (sm && !fsw) continue;
+                    if (fm == 7 && sh != shapes[0]) continue;   // no site-parallel step left to shape
+                    const int f = fm & user_fast, sw = (sm & f & user_sweep) | (bsweep & 8);
+                    cand.push_back({f, sw, sh[0], sh[1], sh[2]});
+                }
         double tbest = INFINITY;
-        std::pair<int, int> best_c = cand[0];
+        Cand best_c = cand[0];
         const bool prof3 = h->prof;
         h->prof = false;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         int rc3 = MPMC_OK;
         for (size_t c = 0; c < cand.size() && !rc3; ++c) {
-            h->use_fast = cand[c].first;
-            h->use_sweep = cand[c].second;
+            h->use_fast = cand[c].f;
+            h->use_sweep = cand[c].sw;
+            h->tune_R = cand[c].R;
+            h->tune_bx = cand[c].bx;
+            h->tune_sl = cand[c].sl;
             if (c == 0) rc3 = mpmc_trace_levels(h, 0x5eedULL, bnb, 0, mean.data(), var.data(), nullptr);   // warm-up
             if (rc3) break;
             cudaEventRecord(e0, h->stream);
@@ -1729,14 +1768,18 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         h->prof = prof3;
-        h->use_fast = best_c.first;
-        h->use_sweep = best_c.second;
+        h->use_fast = best_c.f;
+        h->use_sweep = best_c.sw;
+        h->tune_R = best_c.R;
+        h->tune_bx = best_c.bx;
+        h->tune_sl = best_c.sl;
         if (rc3) return rc3;
     }
     return ensure_ws(h, h->ws, h->storage, bnb);
 }
 
 int mpmc_set_option(mpmc_handle h, int option, int value) {
+    if (h) ++h->gen;
     if (!h) return MPMC_EINVAL;
     switch (option) {
         case MPMC_OPT_TENSOR_CORE_DEFLATION:
@@ -1834,10 +1877,12 @@ int mpmc_deflation_dots(mpmc_handle h, uint64_t seed, int level, int first, int 
 }
 
 int mpmc_set_deflation(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+    if (h) ++h->gen;
     return set_deflation_impl(h, Z, lambda, pair, k, 0);
 }
 
 int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const double* lambda, const int* pair, int k) {
+    if (h) ++h->gen;
     return set_deflation_impl(h, Z, lambda, pair, k, 1);
 }
 
@@ -1912,3 +1957,148 @@ int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, int on_dev
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches of handles
+// The multilevel traces of several independent handles (different lattices,
+// kappas, polynomials) run as parallel branches of one captured CUDA graph:
+// each handle's launches stay on its own stream, forked from and joined to
+// the batch's stream, so that small instances overlap on the GPU and a whole
+// batch costs one graph launch on the host.  The graph is captured on the
+// first call and replayed while the noise block (seed, count, first index)
+// and every handle's state (polynomials, deflation, links, options, block,
+// stream) stay the same; any change recaptures it.
+struct mpmc_batch {
+    std::vector<mpmc_handle> h;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    long long launches = 0;
+    uint64_t key_seed = 0;
+    int key_n = -1, key_first = -1;
+    std::vector<unsigned long long> key_gen;
+    std::vector<int> nbs;
+};
+
+namespace {
+
+void batch_drop_graph(mpmc_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->nodes = 0;
+    b->key_n = -1;
+}
+
+}  // namespace
+
+int mpmc_batch_create(mpmc_batch_handle* out, int n, const mpmc_handle* handles) {
+    if (!out || n < 1 || !handles) return MPMC_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i] || !handles[i]->stream) return MPMC_EINVAL;   // the legacy default stream cannot be captured
+    mpmc_batch* b = new (std::nothrow) mpmc_batch;
+    if (!b) return MPMC_ENOMEM;
+    b->h.assign(handles, handles + n);
+    b->join.assign(n, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i) ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        mpmc_batch_destroy(b);
+        return MPMC_ECUDA;
+    }
+    *out = b;
+    return MPMC_OK;
+}
+
+int mpmc_batch_destroy(mpmc_batch_handle b) {
+    if (!b) return MPMC_EINVAL;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    batch_drop_graph(b);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+    return MPMC_OK;
+}
+
+long long mpmc_batch_launch_count(mpmc_batch_handle b) { return b ? b->launches : -1; }
+
+int mpmc_batch_trace_levels(mpmc_batch_handle b, uint64_t seed, int nsamples, int first, double* mean,
+                            double* var) {
+    if (!b || nsamples < 1 || first < 0) return MPMC_EINVAL;
+    const int n = (int)b->h.size();
+    b->nbs.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        mpmc_ctx* h = b->h[i];
+        if (!h->stream) return fail(h, MPMC_EINVAL, "a batched handle needs its own stream");
+        if (int rc = trace_prepare(h, nsamples, first, &b->nbs[i])) return rc;
+    }
+    bool same = b->exec && b->key_seed == seed && b->key_n == nsamples && b->key_first == first &&
+                b->key_gen.size() == (size_t)n;
+    for (int i = 0; i < n && same; ++i) same = b->key_gen[i] == b->h[i]->gen;
+    if (!same) {
+        batch_drop_graph(b);
+        // one plain run first: lazy allocations and kernel attributes happen outside the capture
+        for (int i = 0; i < n; ++i) {
+            mpmc_ctx* h = b->h[i];
+            const bool prof = h->prof;
+            h->prof = false;
+            const int rc = trace_enqueue(h, seed, nsamples, first, b->nbs[i]);
+            h->prof = prof;
+            if (rc) return rc;
+        }
+        for (int i = 0; i < n; ++i)
+            if (cudaStreamSynchronize(b->h[i]->stream) != cudaSuccess) return cuda_check(b->h[i], cudaGetLastError(), "batch warm-up");
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_check(b->h[0], cudaGetLastError(), "batch capture");
+        int rc = MPMC_OK;
+        cudaError_t e = cudaEventRecord(b->fork, b->origin);
+        for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+            mpmc_ctx* h = b->h[i];
+            e = cudaStreamWaitEvent(h->stream, b->fork, 0);
+            if (e != cudaSuccess) break;
+            const bool prof = h->prof;
+            h->prof = false;
+            const long long l0 = h->launches;
+            rc = trace_enqueue(h, seed, nsamples, first, b->nbs[i]);
+            h->launches = l0;   // captured, not launched: counted at replay
+            h->prof = prof;
+            if (rc) break;
+            e = cudaEventRecord(b->join[i], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(b->origin, &graph);
+        if (rc || e != cudaSuccess || e2 != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            return rc ? rc : fail(b->h[0], MPMC_ECUDA, "batch graph capture failed");
+        }
+        if (cudaGraphGetNodes(graph, nullptr, &b->nodes) != cudaSuccess ||
+            cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            b->exec = nullptr;
+            return fail(b->h[0], MPMC_ECUDA, "batch graph instantiation failed");
+        }
+        cudaGraphDestroy(graph);
+        b->key_seed = seed;
+        b->key_n = nsamples;
+        b->key_first = first;
+        b->key_gen.resize(n);
+        for (int i = 0; i < n; ++i) b->key_gen[i] = b->h[i]->gen;
+    }
+    if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess || cudaStreamSynchronize(b->origin) != cudaSuccess)
+        return cuda_check(b->h[0], cudaGetLastError(), "batch graph launch");
+    b->launches += (long long)b->nodes;
+    for (int i = 0; i < n; ++i) {
+        double* m = mean ? mean + 2 * (size_t)i * MPMC_MAX_POLYS : nullptr;
+        double* v = var ? var + (size_t)i * MPMC_MAX_POLYS : nullptr;
+        if (int rc = trace_collect(b->h[i], nsamples, m, v, nullptr)) return rc;
+    }
+    return MPMC_OK;
+}

@@ -67,6 +67,11 @@ _SIGS = {
     "mpmc_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mpmc_set_deflation_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int]),
+    "mpmc_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]),
+    "mpmc_batch_trace_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_batch_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "mpmc_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "mpmc_deflation_norms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -348,6 +353,50 @@ class Handle:
         self._check(self._L.mpmc_profile_read(self._h, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
                     "mpmc_profile_read")
         return ms.value, n.value, b.value
+
+
+class Batch:
+    """Independent handles whose multilevel traces run as one captured CUDA graph.
+
+    The handles are borrowed: keep them alive (and destroy them) after the
+    batch.  Each needs its own stream (the handles' default).
+    """
+
+    def __init__(self, handles):
+        self._L = lib()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h for h in self.handles])
+        b = ctypes.c_void_p()
+        rc = self._L.mpmc_batch_create(ctypes.byref(b), len(self.handles), ctypes.cast(arr, ctypes.c_void_p))
+        if rc:
+            raise MpmcError(rc, "mpmc_batch_create")
+        self._b = b
+
+    def mpmc_batch_trace_levels(self, seed, nsamples, first=0):
+        """(mean, var) arrays of shape (n_handles, MAX_POLYS); entries past a handle's levels are unused."""
+        n = len(self.handles)
+        mean = np.zeros((n, MAX_POLYS), dtype=np.complex128)
+        var = np.zeros((n, MAX_POLYS), dtype=np.float64)
+        rc = self._L.mpmc_batch_trace_levels(self._b, ctypes.c_uint64(seed), int(nsamples), int(first), _ptr(mean),
+                                             _ptr(var))
+        if rc:
+            msgs = [self._L.mpmc_last_error(h._h).decode() for h in self.handles]
+            raise MpmcError(rc, "mpmc_batch_trace_levels: " + "; ".join(m for m in msgs if m))
+        return mean, var
+
+    def mpmc_batch_launch_count(self):
+        return int(self._L.mpmc_batch_launch_count(self._b))
+
+    def close(self):
+        if self._b is not None:
+            self._L.mpmc_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def mpmc_trace_poly_noalloc(links, kappa, roots, seed, level, first, nsamples, out=None, bc_t=1, stream=None):

@@ -169,3 +169,44 @@ def configure(h, polys, defl, block=None):
             h.mpmc_set_poly(i, kinds[kind], r, o, leja=True)
     if block:
         h.mpmc_set_block(block)
+
+
+# ---------------------------------------------------------------- uneven batch
+BATCH_LATTICES = ((4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 8), (8, 8, 8, 16), (12, 12, 12, 12))
+
+
+def batch_instances(count=64, seed=5, nsamples=32):
+    """`count` independent instances for the batched estimate: lattice drawn
+    from BATCH_LATTICES, kappa ~ U[0.118, 0.124], eps ~ U[0.2, 0.4], near-identity
+    links with their own gauge seed, three levels (composite 20 x 15 = degree
+    299, degree 40, degree 8), no deflation, `nsamples` noises per level."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        dims = BATCH_LATTICES[int(rng.integers(len(BATCH_LATTICES)))]
+        kappa = float(rng.uniform(0.118, 0.124))
+        eps = float(rng.uniform(0.2, 0.4))
+        out.append(Workload(f"batch{i}", dims, "near_identity", 100 + i, round(eps, 4), round(kappa, 5),
+                            (("composite", 15, 20), ("single", 40), ("single", 8)), 0, nsamples, 5000 + i,
+                            6000 + i, block=nsamples))
+    return out
+
+
+def setup_light(h64, wl):
+    """Polynomials of a workload without deflation: one GMRES run for the single
+    polynomials and p_in, PP-GMRES for p_out (Sec. 5, steps 2a and 2c)."""
+    S = krylov_setup.Setup(h64)
+    v0 = synth.random_unit_vector(wl.n, wl.setup_seed)
+    singles = [lv[1] for lv in wl.levels if lv[0] == "single"]
+    inners = [lv[1] - 1 for lv in wl.levels if lv[0] != "single"]
+    degs = sorted(set(singles + inners))
+    roots = dict(zip(degs, S.single_roots(v0, degs)))
+    polys = []
+    for lv in wl.levels:
+        if lv[0] == "single":
+            polys.append(("single", roots[lv[1]], None))
+        else:
+            inner = roots[lv[1] - 1]
+            outer, _ = S.pp_roots(inner, v0, m_out=lv[2])
+            polys.append((lv[0], inner, outer))
+    return polys

@@ -1,0 +1,91 @@
+"""Batches of independent instances (mpmc_batch_*): the multilevel traces of
+handles with different lattices, kappas, polynomials, deflation and
+precision run as parallel branches of one captured CUDA graph.  Each
+handle's means and variances must equal what mpmc_trace_levels returns for
+it alone (same kernels, same launch shapes, same summation order: 1e-13 of
+the level's size), on the capturing call, on a replay, and after a change
+to one handle (which recaptures the graph)."""
+
+import numpy as np
+import pytest
+
+from conftest import links
+from paper_2306_09559_gb300 import build
+from paper_2306_09559_gb300 import mpmc as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    G.lib()
+
+
+def _instances():
+    from test_gpu_parity import set_polys, small_setup
+    op, polys, lam, Z, pair = small_setup()
+    hs = []
+    h = G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, G.FP32, 1)
+    h.mpmc_set_deflation(Z, lam, pair)
+    set_polys(h, polys)
+    h.mpmc_set_block(16)
+    hs.append(h)
+    h = G.Handle(links((2, 4, 2, 4), "near_identity", 5, 0.3), 0.121, G.FP64, -1)
+    h.mpmc_set_poly(0, G.SINGLE, np.linspace(0.6, 1.4, 9) + 0.05j)
+    h.mpmc_set_poly(1, G.SINGLE, np.linspace(0.7, 1.3, 4) + 0.02j)
+    hs.append(h)
+    h = G.Handle(links((6, 4, 4, 2), "near_identity", 6, 0.25), 0.119, G.BF16S, 1)
+    h.mpmc_set_poly(0, G.COMPOSITE, np.linspace(0.6, 1.4, 3) + 0.1j, np.linspace(0.5, 1.5, 4))
+    h.mpmc_set_poly(1, G.SINGLE, np.linspace(0.6, 1.4, 5) + 0.1j)
+    h.mpmc_set_poly(2, G.SINGLE, np.linspace(0.8, 1.2, 2) + 0.1j)
+    h.mpmc_set_block(32)
+    hs.append(h)
+    return hs
+
+
+def _alone(hs, seed, N, first):
+    out = []
+    for h in hs:
+        m, v, _ = h.mpmc_trace_levels(seed, N, first, want_samples=False)
+        out.append((m, v))
+    return out
+
+
+def _compare(mean, var, ref):
+    for i, (m, v) in enumerate(ref):
+        L = m.size
+        scale = np.maximum(np.abs(m), 1.0)
+        assert np.all(np.abs(mean[i, :L] - m) <= 1e-13 * scale), i
+        assert np.allclose(var[i, :L], v, rtol=1e-12, atol=0, equal_nan=True), i
+
+
+def test_batch_matches_each_handle_alone():
+    hs = _instances()
+    try:
+        ref = _alone(hs, 41, 40, 3)
+        with G.Batch(hs) as b:
+            m1, v1 = b.mpmc_batch_trace_levels(41, 40, 3)     # plain run, capture, replay
+            n1 = b.mpmc_batch_launch_count()
+            m2, v2 = b.mpmc_batch_trace_levels(41, 40, 3)     # replay of the same graph
+            n2 = b.mpmc_batch_launch_count()
+            assert n1 > 0 and n2 == 2 * n1
+            _compare(m1, v1, ref)
+            _compare(m2, v2, ref)
+            # a new noise block and a changed handle: the graph is captured again
+            hs[1].mpmc_set_poly(1, G.SINGLE, np.linspace(0.7, 1.3, 6) + 0.02j)
+            ref3 = _alone(hs, 42, 24, 0)
+            m3, v3 = b.mpmc_batch_trace_levels(42, 24, 0)
+            _compare(m3, v3, ref3)
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_batch_rejects_bad_arguments():
+    import ctypes
+    L = G.lib()
+    b = ctypes.c_void_p()
+    assert L.mpmc_batch_create(ctypes.byref(b), 0, None) == G.MPMC_EINVAL
+    assert L.mpmc_batch_trace_levels(None, 1, 4, 0, None, None) == G.MPMC_EINVAL
+    assert L.mpmc_batch_destroy(None) == G.MPMC_EINVAL
