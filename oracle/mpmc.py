@@ -199,3 +199,38 @@ def multilevel_cost(variances, costs, eps):
 def hutchinson_cost(variance, cost, eps):
     """Plain Monte Carlo cost eps^-2 V_0 C_0 (Sec. 5, after Eq. (3))."""
     return float(variance * cost / eps ** 2)
+
+
+def probing_vectors(dims, m, cols):
+    """Probe vectors for the distance colouring of period m (m divides every extent).
+
+    Column q = 12 * colour + e, colour = x%m + m (y%m) + m^2 (z%m) + m^3 (t%m):
+    v_q(site, e') = 1 where the site has that colour and e' = e, else 0.
+    Two sites of one colour differ by a multiple of m in every direction, so
+    they are at least m hops apart on the periodic lattice.
+    """
+    lx, ly, lz, lt = dims
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    colour = ((x % m) + m * (y % m) + m * m * (z % m) + m ** 3 * (t % m)).reshape(-1)
+    V = colour.size
+    out = np.zeros((V, 12, len(cols)), dtype=np.complex128)
+    for j, q in enumerate(cols):
+        c, e = divmod(q, 12)
+        out[colour == c, e, j] = 1.0
+    return out.reshape(12 * V, len(cols))
+
+
+def probing_trace(op, spec, m, defl=None, block=48):
+    """Sum over the 12 m^4 probe vectors of v^H p(A) v: the probing estimate of
+    Tr p(A) (exact when p(A) couples no two sites that are m or more hops apart,
+    i.e. for polynomials of degree below m)."""
+    dims = op.dims
+    if any(L % m for L in dims):
+        raise ValueError("m must divide every lattice extent")
+    total = 0j
+    nq = 12 * m ** 4
+    for q0 in range(0, nq, block):
+        cols = list(range(q0, min(nq, q0 + block)))
+        Vb = probing_vectors(dims, m, cols)
+        total += np.einsum('nr,nr->', Vb.conj(), apply_spec(op, spec, Vb, defl))
+    return total
