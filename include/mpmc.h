@@ -357,6 +357,23 @@ MPMC_API int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const dou
 MPMC_API int mpmc_deflation_norms(mpmc_handle h, double* d);
 
 /*
+ * mpmc_trace_probing: the probing estimate of Tr p(A) for polynomial `index`
+ * (single or composite), used for the lowest-degree level in place of its
+ * Monte Carlo (Sec. 5, step 3c: the trace of the cheapest polynomial can be
+ * found exactly).  Probe vectors: for each colour c of the period-m
+ * colouring colour(x) = x%m + m (y%m) + m^2 (z%m) + m^3 (t%m) and each of the
+ * 12 spin-colour components e, the indicator of {sites of colour c} x {e};
+ * trace = sum over the 12 m^4 vectors of v^H p(A) v (complex, interleaved).
+ * Sites of one colour are m or more hops apart, so the estimate is exact for
+ * polynomials of degree below m, and for any degree when m equals every
+ * extent.  m must divide every lattice extent.  The vectors run through the
+ * same chain kernels as mpmc_apply_poly in blocks of the handle's width; the
+ * in-colour sums are FP64 in a fixed order.  Errors: EINVAL (m), ESTATE (no
+ * polynomial), ENOTSUP (projected composite).
+ */
+MPMC_API int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace);
+
+/*
  * mpmc_vector_stats: for k device vectors z_i (vector-major, complex double,
  * vector i at Z + 2*n*i) writes stats[4i..4i+3] = (|z_i|^2, |A z_i|^2,
  * Re z_i^H A z_i, Im z_i^H A z_i), with A applied in FP64.  These give the

@@ -348,6 +348,70 @@ inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t)
 
 }  // namespace
 
+// ------------------------------------------------------------------ probing
+// Probe vectors of the period-m distance colouring: column q = 12 * colour + e,
+// colour = x%m + m (y%m) + m^2 (z%m) + m^3 (t%m).
+__device__ __forceinline__ int probe_colour(int site, int lx, int ly, int lz, int m) {
+    const int x = site % lx;
+    int r = site / lx;
+    const int y = r % ly;
+    r /= ly;
+    const int z = r % lz;
+    const int t = r / lz;
+    return (x % m) + m * ((y % m) + m * ((z % m) + m * (t % m)));
+}
+
+template <class S>
+__global__ void k_probe_block(int V, int lx, int ly, int lz, int m, int q0, int nq, int nb, S* __restrict__ out) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (site, e, col)
+    if (idx >= (size_t)V * 12 * nb) return;
+    const int col = (int)(idx % nb);
+    const int e = (int)((idx / nb) % 12);
+    const int site = (int)(idx / ((size_t)12 * nb));
+    const int q = q0 + col;
+    const bool one = col < nq && e == q % 12 && probe_colour(site, lx, ly, lz, m) == q / 12;
+    using T = typename Math<S>::T;
+    st(out + idx * 2, cplx<T>{one ? T(1) : T(0), T(0)});
+}
+
+// part[chunk][col] = sum over the chunk's sites of colour c(q) of X[site][e(q)][col] (FP64, site order)
+template <class S>
+__global__ void k_probe_dot(int V, int lx, int ly, int lz, int m, int q0, int nq, int nb, int nchunk,
+                            const S* __restrict__ X, double2* __restrict__ part) {
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.x;
+    if (col >= nb) return;
+    double sr = 0.0, si = 0.0;
+    if (col < nq) {
+        const int q = q0 + col, c = q / 12, e = q % 12;
+        const int per = (V + nchunk - 1) / nchunk;
+        const int s1 = min(V, (chunk + 1) * per);
+        for (int site = chunk * per; site < s1; ++site) {
+            if (probe_colour(site, lx, ly, lz, m) != c) continue;
+            const auto v = ld(X + (((size_t)site * 12 + e) * nb + col) * 2);
+            sr += (double)v.re;
+            si += (double)v.im;
+        }
+    }
+    part[(size_t)chunk * nb + col] = make_double2(sr, si);
+}
+
+// total += sum over columns (in order) of the chunk sums (in order): one thread
+__global__ void k_probe_sum(int nchunk, int nb, int nq, const double2* __restrict__ part, double2* total) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double tr = total->x, ti = total->y;
+    for (int col = 0; col < nq; ++col) {
+        double sr = 0.0, si = 0.0;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            sr += part[(size_t)ch * nb + col].x;
+            si += part[(size_t)ch * nb + col].y;
+        }
+        tr += sr;
+        ti += si;
+    }
+    *total = make_double2(tr, ti);
+}
+
 // ================================================================== host side
 LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R) {
     LaunchCfg c;
@@ -504,6 +568,31 @@ void launch_normalize(size_t n, const double2* w, const double* nrm2, double2* d
 void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k, double2* Z, cudaStream_t s) {
     const dim3 grid(blocks_for(n, 256), k);
     k_combine<<<grid, 256, 0, s>>>(n, m, Vb, Y, k, Z);
+}
+
+}  // namespace mpmc
+
+namespace mpmc {
+
+void launch_probe_block(int storage, const Geom& g, int m, int q0, int nq, int nb, void* out, cudaStream_t s) {
+    const size_t n = (size_t)g.V * 12 * nb;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (storage == ST_F64) k_probe_block<double><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (double*)out);
+    else if (storage == ST_F32) k_probe_block<float><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (float*)out);
+    else k_probe_block<__nv_bfloat16><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (__nv_bfloat16*)out);
+}
+
+void launch_probe_trace(int storage, const Geom& g, int m, int q0, int nq, int nb, const void* X, int nchunk,
+                        double2* part, double2* total, cudaStream_t s) {
+    const dim3 grid(nchunk, (nb + 63) / 64);
+    if (storage == ST_F64)
+        k_probe_dot<double><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk, (const double*)X, part);
+    else if (storage == ST_F32)
+        k_probe_dot<float><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk, (const float*)X, part);
+    else
+        k_probe_dot<__nv_bfloat16><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk,
+                                                      (const __nv_bfloat16*)X, part);
+    k_probe_sum<<<1, 32, 0, s>>>(nchunk, nb, nq, part, total);
 }
 
 }  // namespace mpmc

@@ -214,6 +214,13 @@ void launch_normalize(size_t n, const double2* w, const double* nrm2, double2* d
 void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k, double2* Z, cudaStream_t s);
 // complex double [site][e][1] <-> storage conversions for a single vector are import/export with nb = 1
 
+// Probing (period-m distance colouring): out = probe block of columns q0 .. q0+nq-1
+// (zero beyond nq); total += sum of X over the probe entries of those columns (FP64,
+// fixed order; part: nchunk x nb scratch)
+void launch_probe_block(int storage, const Geom& g, int m, int q0, int nq, int nb, void* out, cudaStream_t s);
+void launch_probe_trace(int storage, const Geom& g, int m, int q0, int nq, int nb, const void* X, int nchunk,
+                        double2* part, double2* total, cudaStream_t s);
+
 int mdot_parts(size_t n);
 
 }  // namespace mpmc

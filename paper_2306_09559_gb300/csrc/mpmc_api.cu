@@ -126,6 +126,8 @@ struct mpmc_ctx {
     double* kr_nrm = nullptr;
     int kr_m = 0;
     long long launches = 0;
+    double2* probe = nullptr;     // probing: [nchunk][nb] partial sums + 1 total
+    size_t probe_cap = 0;
     unsigned long long gen = 0;   // bumped by every call that changes what a trace launches
     // profiling: events around kernel launches of each class (mpmc_profile)
     bool prof = false;
@@ -1030,6 +1032,7 @@ int mpmc_destroy(mpmc_handle h) {
     dev_free(h->links64);
     dev_free(h->links32);
     dev_free(h->links_ex);
+    dev_free(h->probe);
     dev_free(h->samples);
     dev_free(h->io);
     dev_free(h->kr_part);
@@ -1168,6 +1171,45 @@ static int set_deflation_impl(mpmc_handle h, const double* Z, const double* lamb
     }
     if (int rc = dev_alloc(h, &h->d_coef, sizeof(double2) * (size_t)MPMC_MAX_POLYS * k)) return rc;
     return upload_coefficients(h);
+}
+
+int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
+    if (!h) return MPMC_EINVAL;
+    if (!trace || m < 1 || h->g.lx % m || h->g.ly % m || h->g.lz % m || h->g.lt % m)
+        return fail(h, MPMC_EINVAL, "the period m must divide every lattice extent");
+    if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
+    const PolyDef& p = h->polys[index];
+    if (!p.set) return fail(h, MPMC_ESTATE, "polynomial not set");
+    if (p.kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "probing of the projected composite");
+    const long long nq_all = 12LL * m * m * m * m;
+    const int nb = (int)std::min<long long>(default_nb(h), nq_all);
+    if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
+    const int nchunk = 152;
+    const size_t need = (size_t)nchunk * nb + 1;
+    if (h->probe_cap < need) {
+        dev_free(h->probe);
+        h->probe_cap = 0;
+        if (int rc = dev_alloc(h, &h->probe, sizeof(double2) * need)) return rc;
+        h->probe_cap = need;
+    }
+    double2* total = h->probe + (size_t)nchunk * nb;
+    CK(cudaMemsetAsync(total, 0, sizeof(double2), h->stream));
+    Workspace& ws = h->ws;
+    for (long long q0 = 0; q0 < nq_all; q0 += nb) {
+        const int cnt = (int)std::min<long long>(nb, nq_all - q0);
+        launch_probe_block(ws.storage, h->g, m, (int)q0, cnt, nb, ws.r, h->stream);
+        LAUNCHED(1);
+        if (int rc = chain_apply(h, ws, p, ws.r, ws.x)) return rc;
+        launch_probe_trace(ws.storage, h->g, m, (int)q0, cnt, nb, ws.x, nchunk, h->probe, total, h->stream);
+        LAUNCHED(2);
+    }
+    double2 t;
+    CK(cudaMemcpyAsync(&t, total, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (int rc = device_flag(h)) return rc;
+    trace[0] = t.x;
+    trace[1] = t.y;
+    return prof_collect(h);
 }
 
 int mpmc_deflation_norms(mpmc_handle h, double* d) {

@@ -72,6 +72,7 @@ _SIGS = {
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_batch_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "mpmc_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "mpmc_trace_probing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_deflation_norms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -307,6 +308,12 @@ class Handle:
         v = ctypes.c_int()
         self._check(self._L.mpmc_get_option(self._h, int(option), ctypes.byref(v)), "mpmc_get_option")
         return v.value
+
+    def mpmc_trace_probing(self, index, m):
+        """Probing estimate of Tr p(A) (period-m colouring; exact below degree m)."""
+        t = np.zeros(1, dtype=np.complex128)
+        self._check(self._L.mpmc_trace_probing(self._h, int(index), int(m), _ptr(t)), "mpmc_trace_probing")
+        return complex(t[0])
 
     def mpmc_deflation_norms(self):
         """d_i = z_pair(i)^H gamma5 z_i of the stored deflation vectors (complex, length k)."""
