@@ -374,6 +374,17 @@ MPMC_API int mpmc_deflation_norms(mpmc_handle h, double* d);
 MPMC_API int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace);
 
 /*
+ * mpmc_trace_level: one level of mpmc_trace_levels on its own (the same
+ * samples, noise indices first .. first+nsamples-1 of that level), for the
+ * sequential stopping rule of Sec. 5, step 3, which runs the Monte Carlos one
+ * after another, each until its standard error meets its share of the
+ * tolerance.  mean: 1 complex (with the level's exact correction), var: 1,
+ * samples: nsamples complex (optional).  Errors: as mpmc_trace_levels.
+ */
+MPMC_API int mpmc_trace_level(mpmc_handle h, int level, uint64_t seed, int nsamples, int first, double* mean,
+                              double* var, double* samples);
+
+/*
  * mpmc_vector_stats: for k device vectors z_i (vector-major, complex double,
  * vector i at Z + 2*n*i) writes stats[4i..4i+3] = (|z_i|^2, |A z_i|^2,
  * Re z_i^H A z_i, Im z_i^H A z_i), with A applied in FP64.  These give the

@@ -1366,10 +1366,11 @@ int trace_prepare(mpmc_ctx* h, int nsamples, int first, int* nb_out) {
     return MPMC_OK;
 }
 
-int trace_enqueue(mpmc_ctx* h, uint64_t seed, int nsamples, int first, int nb) {
+int trace_enqueue(mpmc_ctx* h, uint64_t seed, int nsamples, int first, int nb, int l0 = 0, int l1 = -1) {
     const int L = num_levels(h);
+    if (l1 < 0) l1 = L;
     Workspace& ws = h->ws;
-    for (int l = 0; l < L; ++l) {
+    for (int l = l0; l < l1; ++l) {
         const bool has_lo = l + 1 < L;
         const bool proj = h->polys[l].kind == MPMC_DEFLATED_COMPOSITE;
         const bool defl = has_lo && h->k > 0;
@@ -1409,17 +1410,19 @@ int trace_enqueue(mpmc_ctx* h, uint64_t seed, int nsamples, int first, int nb) {
     return MPMC_OK;
 }
 
-int trace_collect(mpmc_ctx* h, int nsamples, double* mean, double* var, double* samples) {
+int trace_collect(mpmc_ctx* h, int nsamples, double* mean, double* var, double* samples, int l0 = 0,
+                  int l1 = -1) {
     const int L = num_levels(h);
+    if (l1 < 0) l1 = L;
     const size_t need = (size_t)L * nsamples;
     std::vector<double2> hs(need);
     CK(cudaMemcpyAsync(hs.data(), h->samples, sizeof(double2) * need, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (int rc = prof_collect(h)) return rc;
     if (int rc = device_flag(h)) return rc;
-    for (size_t i = 0; i < need; ++i)
+    for (size_t i = (size_t)l0 * nsamples; i < (size_t)l1 * nsamples; ++i)
         if (!std::isfinite(hs[i].x) || !std::isfinite(hs[i].y)) return fail(h, MPMC_ENONFINITE, "non-finite sample");
-    for (int l = 0; l < L; ++l) {
+    for (int l = l0; l < l1; ++l) {
         const double2* s = hs.data() + (size_t)l * nsamples;
         double mr = 0, mi = 0;
         for (int j = 0; j < nsamples; ++j) { mr += s[j].x; mi += s[j].y; }
@@ -1451,6 +1454,25 @@ int mpmc_trace_levels(mpmc_handle h, uint64_t seed, int nsamples, int first, dou
     if (int rc = trace_prepare(h, nsamples, first, &nb)) return rc;
     if (int rc = trace_enqueue(h, seed, nsamples, first, nb)) return rc;
     return trace_collect(h, nsamples, mean, var, samples);
+}
+
+int mpmc_trace_level(mpmc_handle h, int level, uint64_t seed, int nsamples, int first, double* mean, double* var,
+                     double* samples) {
+    if (!h) return MPMC_EINVAL;
+    const int L = num_levels(h);
+    if (level < 0 || level >= L) return fail(h, MPMC_EINVAL, "level out of range");
+    int nb = 0;
+    if (int rc = trace_prepare(h, nsamples, first, &nb)) return rc;
+    if (int rc = trace_enqueue(h, seed, nsamples, first, nb, level, level + 1)) return rc;
+    std::vector<double> m(2 * (size_t)L), v(L);
+    std::vector<double> all(samples ? 2 * (size_t)L * nsamples : 0);
+    if (int rc = trace_collect(h, nsamples, m.data(), v.data(), samples ? all.data() : nullptr, level, level + 1))
+        return rc;
+    if (mean) { mean[0] = m[2 * level]; mean[1] = m[2 * level + 1]; }
+    if (var) var[0] = v[level];
+    if (samples) std::copy(all.begin() + 2 * (size_t)level * nsamples, all.begin() + 2 * (size_t)(level + 1) * nsamples,
+                           samples);
+    return MPMC_OK;
 }
 
 int mpmc_arnoldi(mpmc_handle h, int op_poly, const double* v0, int m, double* hbar, double* basis, int* steps) {

@@ -73,6 +73,8 @@ _SIGS = {
     "mpmc_batch_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "mpmc_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "mpmc_trace_probing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "mpmc_trace_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_deflation_norms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -314,6 +316,16 @@ class Handle:
         t = np.zeros(1, dtype=np.complex128)
         self._check(self._L.mpmc_trace_probing(self._h, int(index), int(m), _ptr(t)), "mpmc_trace_probing")
         return complex(t[0])
+
+    def mpmc_trace_level(self, level, seed, nsamples, first=0):
+        """(mean with exact correction, variance of Re, samples) of one level."""
+        mean = np.zeros(1, dtype=np.complex128)
+        var = np.zeros(1, dtype=np.float64)
+        samples = np.zeros(nsamples, dtype=np.complex128)
+        rc = self._L.mpmc_trace_level(self._h, int(level), ctypes.c_uint64(seed), int(nsamples), int(first),
+                                      _ptr(mean), _ptr(var), _ptr(samples))
+        self._check(rc, "mpmc_trace_level")
+        return complex(mean[0]), float(var[0]), samples
 
     def mpmc_deflation_norms(self):
         """d_i = z_pair(i)^H gamma5 z_i of the stored deflation vectors (complex, length k)."""
