@@ -357,6 +357,29 @@ MPMC_API int mpmc_set_deflation_device(mpmc_handle h, const double* Z, const dou
 MPMC_API int mpmc_deflation_norms(mpmc_handle h, double* d);
 
 /*
+ * mpmc_solve: x = A^{-1} b for nrhs right-hand sides (layout of
+ * mpmc_apply_poly; host or device per on_device) by restarted GMRES(m) on the
+ * polynomial-preconditioned operator A p_in(A) (Sec. 2.4; polynomial `pin`,
+ * a single polynomial, or pin < 0 for plain GMRES), with a Left-right
+ * Projection with the deflation vectors before every cycle when they are set
+ * (Secs. 2.1 and 5, step 3a).  FP64 handles only.  Stops when
+ * |b - A x| <= rtol |b| or after maxcycles cycles; relres (optional, nrhs)
+ * receives the final relative residuals, matvecs (optional) the products
+ * with A.  Errors: ENOTSUP (precision, p_in kind), EINVAL, ESTATE.
+ *
+ * mpmc_trace_inverse: samples of the level Tr(A^{-1} - p_1(A)) (Sec. 3.1,
+ * Eq. (2); the first Monte Carlo of Sec. 5, step 3a): for Z4 noise b_j
+ * (level id 0xFFFF, noise index first + j), s_j = b_j^H x_j - b_j^H p_1(A) b_j
+ * - sum_i c_i (b_j^H z_i)(u_i^H b_j) with x_j from mpmc_solve and
+ * c_i = 1/lambda_i - p_1(lambda_i); mean (1 complex) adds sum_i c_i.  var: the
+ * variance of Re s; samples optional (nsamples complex).  FP64 handles only.
+ */
+MPMC_API int mpmc_solve(mpmc_handle h, int pin, const double* B, double* X, int nrhs, double rtol, int m,
+                        int maxcycles, int on_device, double* relres, long long* matvecs);
+MPMC_API int mpmc_trace_inverse(mpmc_handle h, int p1, int pin, uint64_t seed, int nsamples, int first, double rtol,
+                                int m, int maxcycles, double* mean, double* var, double* samples);
+
+/*
  * mpmc_trace_probing: the probing estimate of Tr p(A) for polynomial `index`
  * (single or composite), used for the lowest-degree level in place of its
  * Monte Carlo (Sec. 5, step 3c: the trace of the cheapest polynomial can be

@@ -128,6 +128,8 @@ struct mpmc_ctx {
     long long launches = 0;
     double2* probe = nullptr;     // probing: [nchunk][nb] partial sums + 1 total
     size_t probe_cap = 0;
+    double2* sol = nullptr;       // solver: basis (m+1 vectors) and 4 work vectors + coefficients
+    size_t sol_cap = 0;
     unsigned long long gen = 0;   // bumped by every call that changes what a trace launches
     // profiling: events around kernel launches of each class (mpmc_profile)
     bool prof = false;
@@ -1033,6 +1035,7 @@ int mpmc_destroy(mpmc_handle h) {
     dev_free(h->links32);
     dev_free(h->links_ex);
     dev_free(h->probe);
+    dev_free(h->sol);
     dev_free(h->samples);
     dev_free(h->io);
     dev_free(h->kr_part);
@@ -1210,6 +1213,294 @@ int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
     trace[0] = t.x;
     trace[1] = t.y;
     return prof_collect(h);
+}
+
+// ------------------------------------------------------------------ linear equations
+// Right-preconditioned restarted GMRES(m) for A x = b with the operator A p_in(A) (Sec. 2.4:
+// polynomial preconditioning; pin < 0: plain GMRES), FP64, one right-hand side, and a
+// Left-right Projection with the deflation vectors before every cycle (Secs. 2.1, 5 step 3a):
+// x += Z H^{-1} U^H r, r -= A Z H^{-1} U^H r.  b, x: n complex on the device.
+int solve_one(mpmc_ctx* h, int pin, const double2* b, double2* x, double rtol, int m, int maxcycles, double* relres,
+              long long* matvecs) {
+    const size_t n = nsites12(h);
+    Workspace& ws = h->ws64;
+    // solver area: basis V (m+1 vectors), r, t, u, then two caller vectors (b, x), then coefficients
+    double2* Vb = h->sol;
+    double2* r = Vb + (size_t)(m + 1) * n;
+    double2* t = r + n;
+    double2* u = t + n;
+    double2* coef = u + 3 * n;       // m + 2 device coefficients
+    double* part = reinterpret_cast<double*>(h->kr_part);
+    double* nrm = h->kr_nrm;
+    const bool defl = h->k > 0;
+    const long long mv_pin = pin >= 0 ? spec_matvecs(h->polys[pin]) + 1 : 1;
+    auto norm = [&](const double2* v, double* out) -> int {
+        launch_norm2(n, v, part, nrm, h->stream);
+        LAUNCHED(1);
+        double nn = 0;
+        CK(cudaMemcpyAsync(&nn, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        *out = std::sqrt(nn);
+        return MPMC_OK;
+    };
+    auto set_coef = [&](const std::vector<double2>& c) -> int {
+        CK(cudaMemcpyAsync(coef, c.data(), sizeof(double2) * c.size(), cudaMemcpyHostToDevice, h->stream));
+        return MPMC_OK;
+    };
+    // op(v) -> out:  A p_in(A) v  (p_in(A) v left in t when pin >= 0)
+    auto op = [&](const double2* v, double2* out) -> int {
+        const double2* in = v;
+        if (pin >= 0) {
+            if (int e = chain_apply(h, ws, h->polys[pin], v, t)) return e;
+            in = t;
+        }
+        return apply_A(h, ws, in, out);
+    };
+    double bn = 0;
+    if (int e = norm(b, &bn)) return e;
+    CK(cudaMemsetAsync(x, 0, n * 16, h->stream));
+    *matvecs = 0;
+    double rn = bn;
+    for (int cycle = 0; cycle <= maxcycles; ++cycle) {
+        // r = b - A x
+        if (int e = apply_A(h, ws, x, u)) return e;
+        ++*matvecs;
+        CK(cudaMemcpyAsync(r, b, n * 16, cudaMemcpyDeviceToDevice, h->stream));
+        if (int e = set_coef({make_double2(1.0, 0.0)})) return e;
+        launch_maxpy(n, 1, u, coef, r, h->stream);
+        LAUNCHED(1);
+        if (defl) {
+            const int nsplit = gram_nsplit(h->g.V);
+            if (int e = ensure_gram_part(h, (size_t)nsplit * h->k)) return e;
+            launch_block_gram(ST_F64, h->g.V, h->Zb, h->k, ST_F64, r, 1, 1, h->gram_part, nsplit, h->G2, h->stream);
+            launch_proj_coef(h->k, 1, h->d_pair, h->d_invd, h->d_Hinv, nullptr, h->G2, h->D, h->D32, nullptr,
+                             h->stream);
+            launch_rank_update(ST_F64, ST_F64, h->g.V, 1, h->Zb, h->k, h->D, h->D32, 1.0, x, NoiseSpec{0, 0, 0}, x,
+                               h->stream);
+            launch_rank_update(ST_F64, ST_F64, h->g.V, 1, h->Wb, h->k, h->D, h->D32, -1.0, r, NoiseSpec{0, 0, 0}, r,
+                               h->stream);
+            LAUNCHED(4);
+        }
+        if (int e = norm(r, &rn)) return e;
+        if (!(rn > rtol * bn) || cycle == maxcycles || !std::isfinite(rn)) break;
+        // Arnoldi on A p_in(A) from r / |r|, with Givens rotations on the host
+        std::vector<cd> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+        g[0] = rn;
+        CK(cudaMemsetAsync(Vb, 0, n * 16, h->stream));
+        if (int e = set_coef({make_double2(-1.0 / rn, 0.0)})) return e;
+        launch_maxpy(n, 1, r, coef, Vb, h->stream);   // V_0 = r / |r|
+        LAUNCHED(1);
+        std::vector<double2> h1(m + 1), h2(m + 1);
+        int j = 0;
+        for (; j < m; ++j) {
+            double2* vj = Vb + (size_t)j * n;
+            double2* w = Vb + (size_t)(j + 1) * n;
+            if (int e = op(vj, w)) return e;
+            *matvecs += mv_pin;
+            launch_mdot(n, j + 1, Vb, w, h->kr_part, h->kr_h, h->stream);
+            launch_maxpy(n, j + 1, Vb, h->kr_h, w, h->stream);
+            CK(cudaMemcpyAsync(h1.data(), h->kr_h, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, h->stream));
+            launch_mdot(n, j + 1, Vb, w, h->kr_part, h->kr_h + (m + 1), h->stream);
+            launch_maxpy(n, j + 1, Vb, h->kr_h + (m + 1), w, h->stream);
+            CK(cudaMemcpyAsync(h2.data(), h->kr_h + (m + 1), sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost,
+                               h->stream));
+            LAUNCHED(4);
+            double beta = 0;
+            if (int e = norm(w, &beta)) return e;
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cd(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+            H[(size_t)(j + 1) * m + j] = beta;
+            if (beta > 0 && std::isfinite(beta)) {
+                launch_normalize(n, w, nrm, w, h->stream);
+                LAUNCHED(1);
+            }
+            // apply the previous rotations to column j, then a new one
+            for (int i = 0; i < j; ++i) {
+                const cd a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            const cd a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+            const double den = std::sqrt(std::norm(a) + std::norm(c));
+            cs[j] = den > 0 ? a / den : 1.0;
+            sn[j] = den > 0 ? c / den : 0.0;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = std::conj(cs[j]) * g[j];
+            if (std::abs(g[j + 1]) <= rtol * bn || !(beta > 0)) { ++j; break; }
+        }
+        // y = R^{-1} g, x += p_in(A) V y
+        std::vector<cd> y(j);
+        for (int i = j - 1; i >= 0; --i) {
+            cd acc = g[i];
+            for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        std::vector<double2> yc(j);
+        for (int i = 0; i < j; ++i) yc[i] = make_double2(y[i].real(), y[i].imag());
+        if (int e = set_coef(yc)) return e;
+        launch_combine(n, j, Vb, coef, 1, u, h->stream);
+        LAUNCHED(1);
+        const double2* add = u;
+        if (pin >= 0) {
+            if (int e = chain_apply(h, ws, h->polys[pin], u, t)) return e;
+            *matvecs += mv_pin - 1;
+            add = t;
+        }
+        if (int e = set_coef({make_double2(-1.0, 0.0)})) return e;
+        launch_maxpy(n, 1, add, coef, x, h->stream);
+        LAUNCHED(1);
+    }
+    *relres = rn / bn;
+    return MPMC_OK;
+}
+
+int solve_setup(mpmc_ctx* h, int pin, int m) {
+    if (h->storage != ST_F64) return fail(h, MPMC_ENOTSUP, "linear solves run on FP64 handles");
+    if (m < 1 || m > 1024) return fail(h, MPMC_EINVAL, "restart length out of range");
+    if (pin >= MPMC_MAX_POLYS || (pin >= 0 && !h->polys[pin].set)) return fail(h, MPMC_ESTATE, "p_in not set");
+    if (pin >= 0 && h->polys[pin].kind != MPMC_SINGLE) return fail(h, MPMC_ENOTSUP, "p_in must be a single polynomial");
+    const size_t n = nsites12(h);
+    if (int rc = ensure_ws(h, h->ws64, ST_F64, 1)) return rc;
+    const size_t need = (size_t)(m + 6) * n + (m + 2);
+    if (h->sol_cap < need) {
+        dev_free(h->sol);
+        h->sol_cap = 0;
+        if (int rc = dev_alloc(h, &h->sol, sizeof(double2) * need)) return rc;
+        h->sol_cap = need;
+    }
+    if (h->kr_m < m + 1) {
+        dev_free(h->kr_part);
+        dev_free(h->kr_h);
+        dev_free(h->kr_nrm);
+        h->kr_m = 0;
+        const int np = mdot_parts(n);
+        if (int rc = dev_alloc(h, &h->kr_part, sizeof(double2) * (size_t)np * (m + 1))) return rc;
+        if (int rc = dev_alloc(h, &h->kr_h, sizeof(double2) * 2 * (m + 1))) return rc;
+        if (int rc = dev_alloc(h, &h->kr_nrm, sizeof(double) * (np + 1))) return rc;
+        h->kr_m = m + 1;
+    }
+    if (h->k > 0) {
+        if (int rc = ensure_defl_work(h, 1)) return rc;
+        if (int rc = ensure_projection(h)) return rc;
+    }
+    return MPMC_OK;
+}
+
+int mpmc_solve(mpmc_handle h, int pin, const double* B, double* X, int nrhs, double rtol, int m, int maxcycles,
+               int on_device, double* relres, long long* matvecs) {
+    if (!h) return MPMC_EINVAL;
+    if (!B || !X || nrhs < 1 || !(rtol > 0) || maxcycles < 0) return fail(h, MPMC_EINVAL, "bad solve arguments");
+    if (int rc = solve_setup(h, pin, m)) return rc;
+    const size_t n = nsites12(h);
+    const double* src = B;
+    double* dst = X;
+    if (!on_device) {
+        if (int rc = ensure_io(h, n * nrhs)) return rc;
+        CK(cudaMemcpyAsync(h->io, B, n * nrhs * 16, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+        dst = h->io;
+    }
+    double2* b = h->sol + (size_t)(m + 4) * n;
+    double2* x = b + n;
+    long long total_mv = 0;
+    for (int c = 0; c < nrhs; ++c) {
+        launch_import(ST_F64, h->g.V, src, nrhs, c, 1, b, 1, h->stream);
+        LAUNCHED(1);
+        double rr = 0;
+        long long mv = 0;
+        if (int rc = solve_one(h, pin, b, x, rtol, m, maxcycles, &rr, &mv)) return rc;
+        if (relres) relres[c] = rr;
+        total_mv += mv;
+        launch_export(ST_F64, h->g.V, x, 1, dst, nrhs, c, 1, h->stream);
+        LAUNCHED(1);
+    }
+    if (!on_device) CK(cudaMemcpyAsync(X, h->io, n * nrhs * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (matvecs) *matvecs = total_mv;
+    return device_flag(h);
+}
+
+int mpmc_trace_inverse(mpmc_handle h, int p1, int pin, uint64_t seed, int nsamples, int first, double rtol, int m,
+                       int maxcycles, double* mean, double* var, double* samples) {
+    if (!h) return MPMC_EINVAL;
+    if (nsamples < 1 || first < 0 || !(rtol > 0)) return fail(h, MPMC_EINVAL, "bad trace_inverse arguments");
+    if (p1 < 0 || p1 >= MPMC_MAX_POLYS || !h->polys[p1].set) return fail(h, MPMC_ESTATE, "p_1 not set");
+    if (h->polys[p1].kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "p_1 must not be projected");
+    if (int rc = solve_setup(h, pin, m)) return rc;
+    const size_t n = nsites12(h);
+    const int k = h->k;
+    Workspace& ws = h->ws64;
+    // c_i = 1/lambda_i - p_1(lambda_i), divided by d_i for the stored left vectors
+    std::vector<cd> c(k);
+    cd corr = 0.0;
+    for (int i = 0; i < k; ++i) {
+        c[i] = 1.0 / h->lam[i] - spec_value(h->polys[p1], h->lam[i]);
+        corr += c[i];   // sum_i c_i u_i^H z_i with u_i^H z_i = 1
+    }
+    std::vector<cd> s(nsamples);
+    double2* b = h->sol + (size_t)(m + 4) * n;          // solver area (see solve_one)
+    double2* x = b + n;
+    double2* pb = h->sol + (size_t)(m + 3) * n;         // u: free between solves
+    std::vector<double2> g1(k > 0 ? k : 1), g2(k > 0 ? k : 1);
+    double2 dot;
+    for (int j = 0; j < nsamples; ++j) {
+        const NoiseSpec ns{seed, 0xFFFFu, (uint32_t)(first + j)};
+        launch_noise_f64(h->g, ns, 1, 1, 0, reinterpret_cast<double*>(b), h->stream);
+        LAUNCHED(1);
+        double rr = 0;
+        long long mv = 0;
+        if (int rc = solve_one(h, pin, b, x, rtol, m, maxcycles, &rr, &mv)) return rc;
+        // b^H x
+        launch_mdot(n, 1, b, x, h->kr_part, h->kr_h, h->stream);
+        CK(cudaMemcpyAsync(&dot, h->kr_h, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        cd sample(dot.x, dot.y);
+        // b^H p_1(A) b
+        if (int rc = chain_apply(h, ws, h->polys[p1], b, pb)) return rc;
+        launch_mdot(n, 1, b, pb, h->kr_part, h->kr_h, h->stream);
+        CK(cudaMemcpyAsync(&dot, h->kr_h, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+        LAUNCHED(2);
+        CK(cudaStreamSynchronize(h->stream));
+        sample -= cd(dot.x, dot.y);
+        if (k > 0) {
+            // sum_i c_i (b^H z_i)(u_i^H b), u_i = gamma5 z_pair(i) / conj(d_i)
+            const int nsplit = gram_nsplit(h->g.V);
+            if (int rc = ensure_gram_part(h, (size_t)nsplit * k)) return rc;
+            launch_block_gram(ST_F64, h->g.V, h->Zb, k, ST_F64, b, 1, 0, h->gram_part, nsplit, h->G1, h->stream);
+            launch_block_gram(ST_F64, h->g.V, h->Zb, k, ST_F64, b, 1, 1, h->gram_part, nsplit, h->G2, h->stream);
+            LAUNCHED(2);
+            CK(cudaMemcpyAsync(g1.data(), h->G1, sizeof(double2) * k, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaMemcpyAsync(g2.data(), h->G2, sizeof(double2) * k, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            cd dt = 0.0;
+            for (int i = 0; i < k; ++i) {
+                const cd bz = std::conj(cd(g1[i].x, g1[i].y));                  // b^H z_i
+                const int pi = h->pair[i];
+                const cd ub = cd(g2[pi].x, g2[pi].y) / h->dnorm[i];           // u_i^H b
+                dt += c[i] * bz * ub;
+            }
+            sample -= dt;
+        }
+        if (!std::isfinite(sample.real()) || !std::isfinite(sample.imag()))
+            return fail(h, MPMC_ENONFINITE, "non-finite sample");
+        s[j] = sample;
+    }
+    double mr = 0, mi = 0;
+    for (const cd& z : s) { mr += z.real(); mi += z.imag(); }
+    mr /= nsamples;
+    mi /= nsamples;
+    double v = NAN;
+    if (nsamples > 1) {
+        v = 0;
+        for (const cd& z : s) v += (z.real() - mr) * (z.real() - mr);
+        v /= (nsamples - 1);
+    }
+    if (mean) { mean[0] = mr + corr.real(); mean[1] = mi + corr.imag(); }
+    if (var) *var = v;
+    if (samples)
+        for (int j = 0; j < nsamples; ++j) { samples[2 * j] = s[j].real(); samples[2 * j + 1] = s[j].imag(); }
+    return device_flag(h);
 }
 
 int mpmc_deflation_norms(mpmc_handle h, double* d) {

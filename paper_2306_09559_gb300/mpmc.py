@@ -75,6 +75,12 @@ _SIGS = {
     "mpmc_trace_probing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_trace_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mpmc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+    "mpmc_trace_inverse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_deflation_norms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_vector_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -326,6 +332,27 @@ class Handle:
                                       _ptr(mean), _ptr(var), _ptr(samples))
         self._check(rc, "mpmc_trace_level")
         return complex(mean[0]), float(var[0]), samples
+
+    def mpmc_solve(self, B, pin=-1, rtol=1e-10, m=40, maxcycles=50):
+        """x = A^{-1} B (host numpy (n, nrhs) or (n,)); returns (X, relres, matvecs)."""
+        B = _c128(B)
+        nrhs = B.shape[-1] if B.ndim > 1 else 1
+        X = np.empty_like(B)
+        rr = np.zeros(nrhs)
+        mv = ctypes.c_longlong()
+        self._check(self._L.mpmc_solve(self._h, int(pin), _ptr(B), _ptr(X), nrhs, float(rtol), int(m), int(maxcycles),
+                                       0, _ptr(rr), ctypes.byref(mv)), "mpmc_solve")
+        return X, rr, mv.value
+
+    def mpmc_trace_inverse(self, p1, seed, nsamples, first=0, pin=-1, rtol=1e-10, m=40, maxcycles=50):
+        """(mean with exact correction, variance of Re, samples) of Tr(A^{-1} - p_1(A))."""
+        mean = np.zeros(1, dtype=np.complex128)
+        var = np.zeros(1)
+        s = np.zeros(nsamples, dtype=np.complex128)
+        self._check(self._L.mpmc_trace_inverse(self._h, int(p1), int(pin), ctypes.c_uint64(seed), int(nsamples),
+                                               int(first), float(rtol), int(m), int(maxcycles), _ptr(mean), _ptr(var),
+                                               _ptr(s)), "mpmc_trace_inverse")
+        return complex(mean[0]), float(var[0]), s
 
     def mpmc_deflation_norms(self):
         """d_i = z_pair(i)^H gamma5 z_i of the stored deflation vectors (complex, length k)."""
