@@ -472,12 +472,35 @@ def gpu_arm(args):
     def one(h, fst):
         return h.mpmc_trace_levels(wl.noise_seed, wl.nsamples, fst)
 
+    # storage per level: the first level (the one whose samples cancel most) on an FP32-stored
+    # handle, the others on the BF16-stored one
+    h0 = None
+    if len(polys) > 1 and (args.level0_storage == "fp32" or
+                           (args.level0_storage == "auto" and args.precision == "bf16s")):
+        h0 = G.Handle(U, wl.kappa, G.FP32)
+        h0.mpmc_set_stream(stream)
+        workloads.configure(h0, polys, defl, args.block or None)
+        if not args.block:
+            h0.mpmc_autotune(wl.nsamples)
+    handles = [hm] + ([h0] if h0 is not None else [])
+
+    def run_step(fst):
+        if h0 is None:
+            return one(hm, fst)
+        L, N = len(polys), wl.nsamples
+        mean, var, smp = np.zeros(L, dtype=complex), np.zeros(L), np.zeros((L, N), dtype=complex)
+        mean[0], var[0], smp[0] = h0.mpmc_trace_level(0, wl.noise_seed, N, fst)
+        for l in range(1, L):
+            mean[l], var[l], smp[l] = hm.mpmc_trace_level(l, wl.noise_seed, N, fst)
+        return mean, var, smp
+
     for _ in range(args.warmup):
-        one(hm, first)
+        run_step(first)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    l0 = hm.mpmc_launch_count()
-    hm.mpmc_profile(True)
+    l0 = sum(h.mpmc_launch_count() for h in handles)
+    for h in handles:
+        h.mpmc_profile(True)
     results = []
     with ClockSampler(local) as clk:
         barrier()
@@ -487,15 +510,16 @@ def gpu_arm(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
             ev[k][0].record(stream)
-            results.append(one(hm, first))
+            results.append(run_step(first))
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         barrier()
-    launches = hm.mpmc_launch_count() - l0
-    st_ms, st_n, st_bytes = hm.mpmc_profile_read(G.PROF_STENCIL)
-    df_ms, df_n, df_bytes = hm.mpmc_profile_read(G.PROF_DEFLATION)
-    hm.mpmc_profile(False)
+    launches = sum(h.mpmc_launch_count() for h in handles) - l0
+    st_ms, st_n, st_bytes = [sum(x) for x in zip(*[h.mpmc_profile_read(G.PROF_STENCIL) for h in handles])]
+    df_ms, df_n, df_bytes = [sum(x) for x in zip(*[h.mpmc_profile_read(G.PROF_DEFLATION) for h in handles])]
+    for h in handles:
+        h.mpmc_profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(step_ms)
     t_max = t_local
@@ -520,11 +544,12 @@ def gpu_arm(args):
         d2h = 16 * wl.nsamples * len(polys)
 
         def e2e_step():
-            hm.mpmc_set_links(Up)
-            if Zp is not None:
-                hm.mpmc_set_deflation(Zp, lamp, pairp, rows=True)
-            workloads.configure(hm, polys, None)
-            return one(hm, first)
+            for h in handles:
+                h.mpmc_set_links(Up)
+                if Zp is not None:
+                    h.mpmc_set_deflation(Zp, lamp, pairp, rows=True)
+                workloads.configure(h, polys, None)
+            return run_step(first)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -622,6 +647,7 @@ def gpu_arm(args):
             "config": {"workload": wl.describe(), "lattice": "x".join(map(str, wl.dims)),
                        "noises_per_level": wl.nsamples, "levels": [list(x) for x in wl.levels],
                        "deflation_k": wl.k, "nrhs_per_launch": block, "launch_shape": launch,
+                       "level0_storage": "fp32" if h0 is not None else args.precision,
                        "stencil_options": {"fast": fast, "sweep": sweep,
                                            "segment": hm.mpmc_get_option(G.OPT_SWEEP_SEGMENT),
                                            "fast_sites": hm.mpmc_get_option(G.OPT_FAST_SITES)}, "l2": "flushed before every step (256 MB write)",
@@ -651,6 +677,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this build")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--level0-storage", default="auto", choices=["auto", "same", "fp32"],
+                    help="storage of the first level's vectors (auto: fp32 with --precision bf16s)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
