@@ -257,7 +257,7 @@ __global__ void k_tc_reduce(int k, int nb, int Mpad, int Npad, int nsplit, const
 }  // namespace
 
 // ================================================================== host side
-// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda).
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once (no link against libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {

@@ -12,7 +12,7 @@
 
 namespace mpmc {
 
-// cuTensorMapEncodeTiled from the driver entry point table (defl_tc.cu).
+// cuTensorMapEncodeTiled from the CUDA driver entry point table (defl_tc.cu).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 namespace tc {
 

@@ -1,5 +1,5 @@
 """Pins of the probing estimate (the exact trace of the lowest-degree level,
-paper Sec. 5, step 3c and the survey's distance colouring): with m equal to
+paper Sec. 5, step 3c, with a period-m distance colouring): with m equal to
 the lattice extent every probe vector is a unit vector and the estimate is
 the exact trace for any polynomial; for m > degree it is exact as well, since
 p(A) couples only sites fewer than `degree + 1` hops apart; and it differs
