@@ -434,8 +434,8 @@ MPMC_API int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, i
  * batched form of mpmc_trace_levels for many of them.
  *
  * mpmc_batch_create: handles are borrowed (the caller keeps and destroys
- * them, after the batch); each must be on its own stream (not the legacy
- * default stream).  mpmc_batch_trace_levels: noise vectors first ..
+ * them, after the batch); each must be on its own stream (not the legacy or
+ * per-thread default stream, which cannot be captured).  mpmc_batch_trace_levels: noise vectors first ..
  * first+nsamples-1 of every handle (each with its own noise seed `seed`
  * and level ids as in mpmc_trace_levels); mean[2*(i*MPMC_MAX_POLYS + l)]
  * (complex) and var[i*MPMC_MAX_POLYS + l] receive level l of handle i (as

@@ -2350,8 +2350,11 @@ void batch_drop_graph(mpmc_batch* b) {
 int mpmc_batch_create(mpmc_batch_handle* out, int n, const mpmc_handle* handles) {
     if (!out || n < 1 || !handles) return MPMC_EINVAL;
     *out = nullptr;
+    // the legacy default stream (and the per-thread default stream) cannot be captured
     for (int i = 0; i < n; ++i)
-        if (!handles[i] || !handles[i]->stream) return MPMC_EINVAL;   // the legacy default stream cannot be captured
+        if (!handles[i] || !handles[i]->stream || handles[i]->stream == cudaStreamLegacy ||
+            handles[i]->stream == cudaStreamPerThread)
+            return MPMC_EINVAL;
     mpmc_batch* b = new (std::nothrow) mpmc_batch;
     if (!b) return MPMC_ENOMEM;
     b->h.assign(handles, handles + n);
@@ -2389,7 +2392,8 @@ int mpmc_batch_trace_levels(mpmc_batch_handle b, uint64_t seed, int nsamples, in
     b->nbs.assign(n, 0);
     for (int i = 0; i < n; ++i) {
         mpmc_ctx* h = b->h[i];
-        if (!h->stream) return fail(h, MPMC_EINVAL, "a batched handle needs its own stream");
+        if (!h->stream || h->stream == cudaStreamLegacy || h->stream == cudaStreamPerThread)
+            return fail(h, MPMC_EINVAL, "a batched handle needs its own stream");
         if (int rc = trace_prepare(h, nsamples, first, &b->nbs[i])) return rc;
     }
     bool same = b->exec && b->key_seed == seed && b->key_n == nsamples && b->key_first == first &&

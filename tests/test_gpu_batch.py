@@ -89,3 +89,16 @@ def test_batch_rejects_bad_arguments():
     assert L.mpmc_batch_create(ctypes.byref(b), 0, None) == G.MPMC_EINVAL
     assert L.mpmc_batch_trace_levels(None, 1, 4, 0, None, None) == G.MPMC_EINVAL
     assert L.mpmc_batch_destroy(None) == G.MPMC_EINVAL
+
+
+def test_batch_rejects_a_handle_on_the_legacy_default_stream():
+    import ctypes
+    h = G.Handle(links((4, 4, 2, 4), "haar", 0, 0.3), 0.12, G.FP32, 1)
+    try:
+        h.mpmc_set_stream(1)        # cudaStreamLegacy: usable alone, but it cannot be captured
+        L = G.lib()
+        arr = (ctypes.c_void_p * 1)(h._h)
+        b = ctypes.c_void_p()
+        assert L.mpmc_batch_create(ctypes.byref(b), 1, ctypes.cast(arr, ctypes.c_void_p)) == G.MPMC_EINVAL
+    finally:
+        h.close()

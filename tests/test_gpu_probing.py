@@ -51,3 +51,14 @@ def test_probing_rejects_bad_periods():
         with pytest.raises(G.MpmcError) as e:
             h.mpmc_trace_probing(1, 2)
         assert e.value.code == G.MPMC_ESTATE
+
+
+def test_probing_with_one_colour():
+    dims = (4, 2, 2, 4)
+    op = operator(dims, "near_identity", 4, 0.12, 0.3)
+    single = {"kind": "single", "roots": np.linspace(0.8, 1.2, 3) + 0.05j}
+    with G.Handle(links(dims, "near_identity", 4, 0.3), 0.12, G.FP64, 1) as h:
+        h.mpmc_set_poly(0, G.SINGLE, single["roots"], leja=False)
+        got = h.mpmc_trace_probing(0, 1)
+    ref = M.probing_trace(op, single, 1)
+    assert abs(got - ref) <= 1e-12 * abs(ref)

@@ -72,3 +72,22 @@ def test_solve_rejects_reduced_precision():
         with pytest.raises(G.MpmcError) as e:
             h.mpmc_solve(np.ones(12 * 128, dtype=np.complex128))
         assert e.value.code == G.MPMC_ENOTSUP
+
+
+def test_solve_without_cycles_reports_its_residual():
+    """maxcycles = 0: only the Left-right Projection acts, x = Z H^{-1} U^H b.  It is an
+    oblique projection (the residual norm may grow), and what it guarantees is the
+    Petrov-Galerkin condition U^H (b - A x) = 0; the reported relative residual is that
+    of the returned x."""
+    from test_gpu_parity import handle, small_setup
+    op, polys, lam, Z, pair = small_setup()
+    defl = M.Deflation(op, Z, lam, pair)
+    A = dense((4, 4, 4, 4), "haar", 0, 0.12)
+    b = synth.random_block(op.n, 1, 5)[:, 0]
+    with handle((4, 4, 4, 4)) as h:
+        h.mpmc_set_deflation(Z, lam, pair)
+        x, rr, mv = h.mpmc_solve(b, rtol=1e-12, m=10, maxcycles=0)
+    r = b - A @ x
+    res = np.linalg.norm(r) / np.linalg.norm(b)
+    assert abs(rr[0] - res) < 1e-10
+    assert np.max(np.abs(defl.U.conj().T @ r)) < 1e-10 * np.linalg.norm(b) * np.max(np.abs(defl.U))
