@@ -443,7 +443,9 @@ MPMC_API int mpmc_project(mpmc_handle h, const double* B, double* R, int nrhs, i
  * on the first call (after one plain run, which does any lazy allocation)
  * and replayed while (seed, nsamples, first) and every handle's state stay
  * the same; changing a handle (polynomials, deflation, links, options,
- * block, stream, autotune) recaptures it.  mpmc_batch_launch_count: kernel
+ * block, stream, autotune), or any call on it that allocates a device
+ * buffer (a longer trace, an apply or deflation dots with another block
+ * width), recaptures it.  mpmc_batch_launch_count: kernel
  * nodes replayed so far.  Errors: as mpmc_trace_levels, EINVAL (a handle on
  * the legacy default stream), ECUDA (capture or launch failed).
  */

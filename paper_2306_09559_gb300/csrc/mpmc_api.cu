@@ -169,6 +169,10 @@ int cuda_check(mpmc_ctx* h, cudaError_t e, const char* what) {
         if (rc__) return rc__;                                         \
     } while (0)
 
+// Every device buffer of a handle comes from here.  A new allocation bumps the
+// handle's generation: a captured batch graph holds the addresses of the
+// buffers it was recorded with, and a buffer freed and allocated again (by any
+// call on the handle between two batch calls) must force a recapture.
 template <class P> int dev_alloc(mpmc_ctx* h, P** p, size_t bytes) {
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
@@ -177,6 +181,7 @@ template <class P> int dev_alloc(mpmc_ctx* h, P** p, size_t bytes) {
         return fail(h, MPMC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
     }
     *p = reinterpret_cast<P*>(q);
+    if (h) ++h->gen;
     return MPMC_OK;
 }
 

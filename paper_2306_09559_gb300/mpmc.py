@@ -454,14 +454,31 @@ def mpmc_trace_poly_noalloc(links, kappa, roots, seed, level, first, nsamples, o
     asynchronous on `stream`).  Returns the samples (host array or `out`).
     """
     L = lib()
-    lt, lz, ly, lx = links.shape[1:5]
+    if len(links.shape) != 7 or tuple(links.shape[0:1]) + tuple(links.shape[5:]) != (4, 3, 3):
+        raise ValueError("links must have shape (4, Lt, Lz, Ly, Lx, 3, 3)")
+    lt, lz, ly, lx = (int(e) for e in links.shape[1:5])
     dims = (ctypes.c_int * 4)(lx, ly, lz, lt)
     r = _c128(roots)
     on_dev = 1 if out is not None else 0
     if on_dev:
+        # the library reads links and writes out through raw device pointers: both must be
+        # contiguous complex128 CUDA tensors of the stated sizes on one device
+        for name, t in (("links", links), ("out", out)):
+            if not _is_device(t):
+                raise ValueError(f"with out= given, {name} must be a CUDA tensor")
+            if str(t.dtype) != "torch.complex128" or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex128 tensor")
+        if links.device != out.device:
+            raise ValueError("links and out must be on the same device")
+        if links.numel() != 36 * lx * ly * lz * lt:
+            raise ValueError("links has the wrong number of entries")
+        if out.numel() < nsamples:
+            raise ValueError(f"out holds {out.numel()} entries, fewer than nsamples = {nsamples}")
         res = out
         lk = links
     else:
+        if _is_device(links):
+            raise ValueError("device links need a device result: pass out=")
         res = np.zeros(nsamples, dtype=np.complex128)
         lk = _c128(links)
     raw = getattr(stream, "cuda_stream", stream)

@@ -82,6 +82,32 @@ def test_batch_matches_each_handle_alone():
             h.close()
 
 
+def test_batch_recaptures_after_plain_calls_reallocate_buffers():
+    """Plain calls on a batched handle (a longer trace, an apply with a narrower
+    block, deflation dots) free and reallocate buffers the captured graph was
+    recorded with; the next identical batch call must recapture, not replay
+    kernels on the old addresses."""
+    hs = _instances()
+    rng = np.random.default_rng(3)
+    try:
+        ref = _alone(hs, 41, 40, 3)
+        with G.Batch(hs) as b:
+            m1, v1 = b.mpmc_batch_trace_levels(41, 40, 3)
+            _compare(m1, v1, ref)
+            hs[0].mpmc_trace_levels(9, 300, 0, want_samples=False)          # longer sample buffer
+            for h in (hs[0], hs[2]):                                         # narrower work block
+                B = rng.standard_normal((h.n, 3)) + 1j * rng.standard_normal((h.n, 3))
+                h.mpmc_apply_poly(1, B)
+            hs[0].mpmc_deflation_dots(5, 1, 0, 7, hs[0].k)                  # other deflation width
+            m2, v2 = b.mpmc_batch_trace_levels(41, 40, 3)
+            _compare(m2, v2, ref)
+            m3, v3 = b.mpmc_batch_trace_levels(41, 40, 3)                   # replay of the new graph
+            _compare(m3, v3, ref)
+    finally:
+        for h in hs:
+            h.close()
+
+
 def test_batch_rejects_bad_arguments():
     import ctypes
     L = G.lib()
