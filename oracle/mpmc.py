@@ -234,3 +234,57 @@ def probing_trace(op, spec, m, defl=None, block=48):
         Vb = probing_vectors(dims, m, cols)
         total += np.einsum('nr,nr->', Vb.conj(), apply_spec(op, spec, Vb, defl))
     return total
+
+
+def torus_distance(dims, a, b):
+    """Hop distance between sites a and b (site index x fastest) of the periodic
+    lattice: the sum over directions of the shorter way round."""
+    d = 0
+    for L in dims:
+        xa, xb = a % L, b % L
+        a, b = a // L, b // L
+        r = abs(xa - xb)
+        d += min(r, L - r)
+    return d
+
+
+def distance_colouring(dims, distance):
+    """A distance-`distance` colouring of the graph of A (Sec. 3.1, choice of
+    p_3): sites whose hop distance on the periodic lattice is at most
+    `distance` receive different colours.  Plain greedy colouring in site
+    order, every earlier site checked by its hop distance (small lattices
+    only).  Returns (colours as an int array of V entries, number of colours)."""
+    V = int(np.prod(dims))
+    colours = np.full(V, -1, dtype=np.int64)
+    for s in range(V):
+        taken = {colours[r] for r in range(s) if torus_distance(dims, s, r) <= distance}
+        c = 0
+        while c in taken:
+            c += 1
+        colours[s] = c
+    return colours, int(colours.max()) + 1
+
+
+def probing_vectors_colours(colours, cols):
+    """Probe vectors of an arbitrary site colouring: column q = 12 c + e is the
+    indicator of {sites of colour c} x {spin-colour component e}."""
+    colours = np.asarray(colours)
+    V = colours.size
+    out = np.zeros((V, 12, len(cols)), dtype=np.complex128)
+    for j, q in enumerate(cols):
+        c, e = divmod(q, 12)
+        out[colours == c, e, j] = 1.0
+    return out.reshape(12 * V, len(cols))
+
+
+def probing_trace_colours(op, spec, colours, ncolours, defl=None, block=48):
+    """Sum over the 12 * ncolours probe vectors of v^H p(A) v.  Exact when no
+    two sites of one colour are coupled by p(A), i.e. when same-coloured sites
+    are more hops apart than the degree of p."""
+    total = 0j
+    nq = 12 * ncolours
+    for q0 in range(0, nq, block):
+        cols = list(range(q0, min(nq, q0 + block)))
+        Vb = probing_vectors_colours(colours, cols)
+        total += np.einsum('nr,nr->', Vb.conj(), apply_spec(op, spec, Vb, defl))
+    return total
