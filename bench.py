@@ -5,9 +5,10 @@ One step = one pass over every level of the multilevel trace estimate
 (Eq. (2)) for one batch of Z4 noise vectors: the composite and single
 polynomial chains fused into the Wilson stencil, the deflation dots, the
 per-sample assembly and the per-level statistics, all through the C ABI
-(mpmc_trace_levels).  Default workload: the 8^4 lattice with levels
-composite 20x10 (degree 199), degree 50 and degree 10, 50 deflation
-eigenpairs and 512 noise vectors per level.
+(mpmc_trace_levels).  Default workload: the near-critical 24^3 x 32 lattice
+(kappa 0.124) with the projected composite 50 x 20 (degree 999), degree 100
+and degree 16, 100 deflation eigenpairs, 64 noise vectors per level, FP32
+against the FP64 path at equal trace standard error.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the host cores instead (bounded sample of the same workload).
@@ -99,7 +100,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ oracle leg
 def oracle_worker(spec):
-    """Runs in a fresh single-threaded process: the oracle, as it stands, on a bounded sample."""
+    """Runs in a fresh single-threaded process: the oracle, as it stands, on a bounded sample
+    (worker w of a pool draws its own noise vectors)."""
     import numpy as np
     from oracle import krylov as K
     from oracle import mpmc as M
@@ -138,7 +140,7 @@ def oracle_worker(spec):
         from oracle import polynomial as P
         d = min(lv[1] for lv in wl.levels if lv[0] == "single")
         roots = np.linspace(1.0, 2.0, d + 1) + 0.1j
-        b = philox.z4_block(wl.noise_seed, len(wl.levels) - 1, 0, 1, wl.V)
+        b = philox.z4_block(wl.noise_seed, len(wl.levels) - 1, spec.get("worker", 0), 1, wl.V)
         times = []
         for step in range(spec["steps"]):
             t1 = time.perf_counter()
@@ -175,8 +177,8 @@ def oracle_worker(spec):
     for step in range(spec["steps"]):
         t1 = time.perf_counter()
         for level in range(len(polys)):
-            M.level_sample_parts(op, polys, level, wl.noise_seed, per_level, defl, first=step * per_level,
-                                 block=per_level)
+            first = (spec.get("worker", 0) * spec["steps"] + step) * per_level
+            M.level_sample_parts(op, polys, level, wl.noise_seed, per_level, defl, first=first, block=per_level)
         times.append(time.perf_counter() - t1)
     applies = per_level * (2 * (len(polys) - 1) + 1)
     return {"times": times, "applies_per_step": applies, "setup_s": t_setup,
@@ -188,20 +190,52 @@ def P_leja(r):
     return P.leja_order(r)
 
 
-def run_oracle(workload, per_level, steps):
-    """The oracle leg in a subprocess with one BLAS/OpenMP thread (cores = 1)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def start_oracle_pool(workload, per_level, steps, cores):
+    """One single-threaded oracle process per host core (spawned fresh, no GPU), each on its
+    own noise vectors (worker w starts at noise index w * per_level)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    with tempfile.NamedTemporaryFile("r", suffix=".json", delete=False) as f:
-        path = f.name
-    spec = json.dumps({"workload": workload, "per_level": per_level, "steps": steps, "out": path})
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec], env=env,
-                       capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("oracle worker failed:\n" + r.stderr[-4000:])
-    out = json.load(open(path))
-    os.unlink(path)
-    return out
+    procs = []
+    for w in range(cores):
+        with tempfile.NamedTemporaryFile("r", suffix=".json", delete=False) as f:
+            path = f.name
+        spec = json.dumps({"workload": workload, "per_level": per_level, "steps": steps, "out": path,
+                           "worker": w})
+        procs.append((subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec], env=env,
+                                       stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True), path))
+    return procs
+
+
+def finish_oracle_pool(procs):
+    """Aggregate rate of the pool: all workers' applies over the slowest worker's time, per step."""
+    outs, errs = [], []
+    for proc, path in procs:
+        _, err = proc.communicate()
+        if proc.returncode == 0:
+            outs.append(json.load(open(path)))
+        else:
+            errs.append(err[-300:])
+        if os.path.exists(path):
+            os.unlink(path)
+    if errs:
+        raise RuntimeError("oracle worker failed:\n" + errs[0])
+    nsteps = min(len(o["times"]) for o in outs)
+    step_times = [max(o["times"][k] for o in outs) for k in range(nsteps)]
+    applies = sum(o["applies_per_step"] for o in outs)
+    return {"step_times": step_times, "applies_per_step": applies, "sample": outs[0]["sample"],
+            "workers": len(outs)}
+
+
+def run_oracle(workload, per_level, steps, cores=None):
+    """The oracle leg on every host core (one single-threaded process per core)."""
+    return finish_oracle_pool(start_oracle_pool(workload, per_level, steps, cores or host_cores()))
 
 
 def cpu_model():
@@ -215,6 +249,19 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
+def cpu_baseline(workload, per_level, steps):
+    """The cpu_baseline object: the oracle, as it stands, on every core of the host."""
+    cores = host_cores()
+    try:
+        r = run_oracle(workload, per_level, steps, cores)
+    except RuntimeError as e:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": "failed: " + str(e)[-300:]}
+    t = r["step_times"]
+    return {"value": r["applies_per_step"] * len(t) / sum(t), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{r['sample']}, on each of {r['workers']} single-threaded processes in parallel "
+                      f"(FP64 numpy oracle, {cpu_model()})"}
+
+
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -223,16 +270,18 @@ def reference_arm(args):
     from paper_2306_09559_gb300 import workloads
     wl = workloads.get(args.workload) if args.workload != BATCH_KEY else None
     per_level = args.oracle_noises
-    res = run_oracle(args.workload, per_level, args.steps + args.warmup)
-    times = res["times"][args.warmup:]
+    cores = host_cores()
+    res = run_oracle(args.workload, per_level, args.steps + args.warmup, cores)
+    times = res["step_times"][args.warmup:]
     value = res["applies_per_step"] * len(times) / sum(times)
+    sample = (f"{res['sample']}, on each of {res['workers']} single-threaded processes (FP64 numpy oracle, "
+              f"{cpu_model()})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.describe() if wl else BATCH_DESC, "sample": res["sample"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{res['sample']} (FP64 numpy oracle, 1 thread, {cpu_model()})"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -260,16 +309,10 @@ def batch_arm(args):
         if dist is not None:
             dist.barrier()
 
-    oracle_proc = None
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-                   CUDA_VISIBLE_DEVICES="")
-        tmp = tempfile.NamedTemporaryFile("r", suffix=".json", delete=False)
-        tmp.close()
-        spec = json.dumps({"workload": BATCH_KEY, "per_level": 1, "steps": 1, "out": tmp.name})
-        oracle_proc = (subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
-                                        env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True),
-                       tmp.name)
+        # the oracle on every host core, before any GPU work (bounded sample, single-threaded processes)
+        cpu = cpu_baseline(BATCH_KEY, 1, 1)
 
     from paper_2306_09559_gb300 import build, workloads
     from paper_2306_09559_gb300 import mpmc as G
@@ -377,17 +420,6 @@ def batch_arm(args):
                 "hbm_peak_source": src, "algorithmic_bytes_per_step": alg,
                 "note": "step-level: every launch of the 64 instances counted, timed as one graph; the working "
                         "set of most instances is L2-resident"}
-    cpu = None
-    if oracle_proc is not None:
-        proc, path = oracle_proc
-        _, err = proc.communicate()
-        if proc.returncode == 0:
-            r = json.load(open(path))
-            cpu = {"value": r["applies_per_step"] / r["times"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{r['sample']}; FP64 numpy oracle, 1 thread, {cpu_model()}"}
-        else:
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
-        os.unlink(path)
     if rank == 0:
         lat = {}
         for w in insts:
@@ -435,18 +467,10 @@ def gpu_arm(args):
         if dist is not None:
             dist.barrier()
 
-    # the oracle process for the CPU baseline is started before any GPU work
-    oracle_proc = None
+    # the oracle on every host core, before any GPU work (bounded sample, single-threaded processes)
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-                   CUDA_VISIBLE_DEVICES="")
-        tmp = tempfile.NamedTemporaryFile("r", suffix=".json", delete=False)
-        tmp.close()
-        spec = json.dumps({"workload": args.workload, "per_level": args.oracle_noises, "steps": 1,
-                           "out": tmp.name})
-        oracle_proc = (subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
-                                        env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True),
-                       tmp.name)
+        cpu = cpu_baseline(args.workload, args.oracle_noises, 1)
 
     from paper_2306_09559_gb300 import build, workloads
     from paper_2306_09559_gb300 import mpmc as G
@@ -472,26 +496,36 @@ def gpu_arm(args):
     def one(h, fst):
         return h.mpmc_trace_levels(wl.noise_seed, wl.nsamples, fst)
 
-    # storage per level: the first level (the one whose samples cancel most) on an FP32-stored
-    # handle, the others on the BF16-stored one
-    h0 = None
-    if len(polys) > 1 and (args.level0_storage == "fp32" or
-                           (args.level0_storage == "auto" and args.precision == "bf16s")):
-        h0 = G.Handle(U, wl.kappa, G.FP32)
-        h0.mpmc_set_stream(stream)
-        workloads.configure(h0, polys, defl, args.block or None)
+    # storage per level: levels whose samples cancel most (the polynomial differences of high
+    # degree) on FP32-stored handles, the others on the handle of --precision
+    codes = {"fp32": G.FP32, "bf16s": G.BF16S, "fp64": G.FP64}
+    if args.level_storage == "auto":
+        per_level = (["fp32", "fp32"] + [args.precision] * len(polys))[:len(polys)] \
+            if args.precision == "bf16s" else [args.precision] * len(polys)
+    else:
+        per_level = args.level_storage.split(",")
+        if len(per_level) != len(polys) or any(x not in codes for x in per_level):
+            raise SystemExit(f"--level-storage needs {len(polys)} entries from {sorted(codes)}")
+    level_handle = {}
+    for name in sorted(set(per_level)):
+        if name == args.precision:
+            level_handle[name] = hm
+            continue
+        hx = G.Handle(U, wl.kappa, codes[name])
+        hx.mpmc_set_stream(stream)
+        workloads.configure(hx, polys, defl, args.block or None)
         if not args.block:
-            h0.mpmc_autotune(wl.nsamples)
-    handles = [hm] + ([h0] if h0 is not None else [])
+            hx.mpmc_autotune(wl.nsamples)
+        level_handle[name] = hx
+    handles = [hm] + [h for h in level_handle.values() if h is not hm]
 
     def run_step(fst):
-        if h0 is None:
+        if len(handles) == 1:
             return one(hm, fst)
         L, N = len(polys), wl.nsamples
         mean, var, smp = np.zeros(L, dtype=complex), np.zeros(L), np.zeros((L, N), dtype=complex)
-        mean[0], var[0], smp[0] = h0.mpmc_trace_level(0, wl.noise_seed, N, fst)
-        for l in range(1, L):
-            mean[l], var[l], smp[l] = hm.mpmc_trace_level(l, wl.noise_seed, N, fst)
+        for l in range(L):
+            mean[l], var[l], smp[l] = level_handle[per_level[l]].mpmc_trace_level(l, wl.noise_seed, N, fst)
         return mean, var, smp
 
     for _ in range(args.warmup):
@@ -518,6 +552,11 @@ def gpu_arm(args):
     launches = sum(h.mpmc_launch_count() for h in handles) - l0
     st_ms, st_n, st_bytes = [sum(x) for x in zip(*[h.mpmc_profile_read(G.PROF_STENCIL) for h in handles])]
     df_ms, df_n, df_bytes = [sum(x) for x in zip(*[h.mpmc_profile_read(G.PROF_DEFLATION) for h in handles])]
+    per_kernel = {}
+    for cls, name in G.PROF_KERNEL_NAMES.items():
+        ms_k, n_k, b_k = [sum(x) for x in zip(*[h.mpmc_profile_read(cls) for h in handles])]
+        if n_k:
+            per_kernel[name] = {"ms": ms_k, "launches": n_k, "bytes": b_k}
     for h in handles:
         h.mpmc_profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -592,14 +631,59 @@ def gpu_arm(args):
                 "paired_mean_diff_over_se": [float(abs(np.mean(d[l].real)) / np.sqrt(v64[l] / wl.nsamples))
                                              for l in range(len(polys))],
                 "paired_std_diff_over_std": [float(np.std(d[l].real) / np.sqrt(v64[l])) for l in range(len(polys))],
+                # bias bound on identical noise: |mean d| <= 0.1 SE_64 + 3 std(d) / sqrt(N)
+                "paired_bias_allowed_over_se": [float((0.1 * np.sqrt(v64[l] / wl.nsamples)
+                                                       + 3 * np.std(d[l].real, ddof=1) / np.sqrt(wl.nsamples))
+                                                      / np.sqrt(v64[l] / wl.nsamples)) for l in range(len(polys))],
+                "paired_bias_within_bound": [bool(abs(np.mean(d[l].real)) <= 0.1 * np.sqrt(v64[l] / wl.nsamples)
+                                                  + 3 * np.std(d[l].real, ddof=1) / np.sqrt(wl.nsamples))
+                                             for l in range(len(polys))],
                 "level_estimates_fp64": [[float(z.real), float(z.imag)] for z in m64],
                 "level_estimates_mixed": [[float(z.real), float(z.imag)] for z in m32]}
 
+    # ---------------------------------------------------------- the rest of the paper's estimate (Eq. (2))
+    # Tr(A^{-1} - M_1), the first Monte Carlo of Sec. 5 step 3a: deflated PP-GMRES solves (FP64) on a
+    # few noise vectors; and Tr(p_3) by probing with a distance-4 colouring for a degree-4 p_3 (Sec. 3.1).
+    # Both run after the timed region on the same handles (polynomial slots 6 and 5 leave the levels alone).
+    extra = {}
+    if not args.no_inverse and defl is not None and polys[0][0] == "deflated_composite":
+        h64.mpmc_set_poly(6, G.SINGLE, polys[0][1], leja=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        mi, vi, si = h64.mpmc_trace_inverse(0, wl.noise_seed, args.inverse_noises, first, pin=6, rtol=1e-8, m=40,
+                                            maxcycles=200)
+        torch.cuda.synchronize()
+        ti = time.perf_counter() - t1
+        extra["inverse_level"] = {"level": "Tr(A^-1 - M_1), deflated PP(%d)-GMRES(40) solves to 1e-8, FP64"
+                                  % len(polys[0][1]), "noises": args.inverse_noises,
+                                  "seconds_per_noise": ti / args.inverse_noises,
+                                  "sample_var": vi if args.inverse_noises > 1 else None,
+                                  "estimate": [mi.real, mi.imag]}
+    if not args.no_probing:
+        from paper_2306_09559_gb300 import krylov_setup, synth
+        p4 = krylov_setup.Setup(h64).single_roots(synth.random_unit_vector(wl.n, wl.setup_seed), [4])[0]
+        colours, nc = G.mpmc_colouring(wl.dims, 4)
+        hm.mpmc_set_poly(5, G.SINGLE, p4, leja=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        tr = hm.mpmc_trace_probing_colours(5, colours, nc)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t1
+        extra["probing"] = {"polynomial": "degree 4 (GMRES harmonic Ritz roots)", "colouring": "distance 4",
+                            "colours": nc, "probe_vectors": 12 * nc, "seconds": tp, "trace": [tr.real, tr.imag],
+                            "period_8_probe_vectors": 12 * 8 ** 4}
+
     # ---------------------------------------------------------- roofline of the dominant kernel
     hbm, sm_max, src = peaks()
-    avg_ms = st_ms / max(st_n, 1)
-    bytes_per_launch = st_bytes / max(st_n, 1)
+    # the dominant kernel: the stencil kernel with the largest share of the timed steps
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dk = per_kernel[dom]
+    avg_ms = dk["ms"] / dk["launches"]
+    bytes_per_launch = dk["bytes"] / dk["launches"]
     achieved_gbs = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+    kernel_mix = {k: {"share_of_step": v["ms"] / t_local, "launches": v["launches"],
+                      "avg_launch_ms": v["ms"] / v["launches"],
+                      "achieved_gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9} for k, v in per_kernel.items()}
     # FP32 pipe: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock, against the
     # algorithmic flops of one step per site and right-hand side
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
@@ -608,7 +692,7 @@ def gpu_arm(args):
     t_hbm, t_alu = bytes_per_launch / (hbm * 1e9), flops_per_launch / (alu_peak * 1e12)
     fast, sweep = hm.mpmc_get_option(G.OPT_FAST_STENCIL), hm.mpmc_get_option(G.OPT_SWEEP_STENCIL)
     # step classes: 1 dotted steps, 2 undotted inner steps, 4 outer steps of composite chains
-    kernel = (f"fused stencil steps: issue-lean k_fast/k_fsweep for class mask {fast} "
+    kernel = (f"{dom} (fused stencil step); issue-lean kernels for step-class mask {fast} "
               f"(t-sweep mask {sweep & fast & 7}), site-parallel k_step/k_outer"
               f"{' (k_sweep form)' if sweep & 8 else ''} for the others")
     alu = {"achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak,
@@ -619,23 +703,12 @@ def gpu_arm(args):
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": args.traffic, "alu": alu}
-    roofline.update({"kernel": kernel, "hbm_peak_source": src, "avg_launch_ms": avg_ms, "launches": st_n,
-                     "share_of_step": st_ms / t_local if t_local else None,
-                     "algorithmic_bytes_per_launch": bytes_per_launch})
-
-    cpu = None
-    if oracle_proc is not None:
-        proc, path = oracle_proc
-        _, err = proc.communicate()
-        if proc.returncode == 0:
-            res = json.load(open(path))
-            tt = res["times"]
-            cpu = {"value": res["applies_per_step"] * len(tt) / sum(tt), "unit": UNIT, "cores": 1,
-                   "kind": "oracle",
-                   "sample": f"{res['sample']}; FP64 numpy oracle, 1 thread, {cpu_model()}"}
-        else:
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
-        os.unlink(path)
+    roofline.update({"kernel": kernel, "hbm_peak_source": src, "avg_launch_ms": avg_ms, "launches": dk["launches"],
+                     "share_of_step": dk["ms"] / t_local if t_local else None,
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "kernel_mix": kernel_mix,
+                     "all_stencil_launches": {"launches": st_n, "avg_launch_ms": st_ms / max(st_n, 1),
+                                              "achieved_gbs": st_bytes / (st_ms / 1000.0) / 1e9,
+                                              "share_of_step": st_ms / t_local}})
 
     if rank == 0:
         clocks = clk.summary()
@@ -647,7 +720,7 @@ def gpu_arm(args):
             "config": {"workload": wl.describe(), "lattice": "x".join(map(str, wl.dims)),
                        "noises_per_level": wl.nsamples, "levels": [list(x) for x in wl.levels],
                        "deflation_k": wl.k, "nrhs_per_launch": block, "launch_shape": launch,
-                       "level0_storage": "fp32" if h0 is not None else args.precision,
+                       "level_storage": per_level,
                        "stencil_options": {"fast": fast, "sweep": sweep,
                                            "segment": hm.mpmc_get_option(G.OPT_SWEEP_SEGMENT),
                                            "fast_sites": hm.mpmc_get_option(G.OPT_FAST_SITES)}, "l2": "flushed before every step (256 MB write)",
@@ -655,6 +728,7 @@ def gpu_arm(args):
                        "setup_s": t_setup},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "dslash_hbm_gbs": achieved_gbs, "cpu_baseline": cpu, "fp64": fp64,
+            **extra,
             "deflation_kernel": {"ms_per_step": df_ms / args.steps, "launches": df_n,
                                  "achieved_gbs": (df_bytes / (df_ms / 1000.0) / 1e9) if df_ms else None},
         }
@@ -670,16 +744,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpmc", choices=["mpmc", "reference"])
-    ap.add_argument("--workload", default="8^4")
+    ap.add_argument("--workload", default="24^3x32")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16s", "fp64"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--oracle-noises", type=int, default=2)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture of this build")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--level0-storage", default="auto", choices=["auto", "same", "fp32"],
-                    help="storage of the first level's vectors (auto: fp32 with --precision bf16s)")
+    ap.add_argument("--level-storage", default="auto",
+                    help="vector storage per level, e.g. fp32,fp32,bf16s (auto: levels 0 and 1 in fp32 "
+                         "with --precision bf16s, else all in --precision)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-inverse", action="store_true", help="skip timing the Tr(A^-1 - M_1) level")
+    ap.add_argument("--inverse-noises", type=int, default=2)
+    ap.add_argument("--no-probing", action="store_true", help="skip timing the probing of a degree-4 p_3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()

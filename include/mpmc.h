@@ -249,9 +249,13 @@ MPMC_API int mpmc_set_links(mpmc_handle h, const double* links);
  * (vector reads and writes counted once per launch, links once per launch,
  * deflation vectors once per launch) accumulate until mpmc_profile(h, 1)
  * clears them; mpmc_profile(h, 0) stops recording.  mpmc_profile_read
- * synchronises the stream and returns the totals of one class.
+ * synchronises the stream and returns the totals of one class.  The
+ * stencil launches are also counted by kernel: the t-sweep issue-lean kernel
+ * (MPMC_PROF_K_FSWEEP), the issue-lean one (K_FAST), the site-parallel one
+ * (K_SITE) and the t-sweep site-parallel one (K_SWEEP).
  */
-enum { MPMC_PROF_STENCIL = 0, MPMC_PROF_DEFLATION = 1, MPMC_PROF_OTHER = 2 };
+enum { MPMC_PROF_STENCIL = 0, MPMC_PROF_DEFLATION = 1, MPMC_PROF_OTHER = 2, MPMC_PROF_K_FSWEEP = 3,
+       MPMC_PROF_K_FAST = 4, MPMC_PROF_K_SITE = 5, MPMC_PROF_K_SWEEP = 6 };
 MPMC_API int mpmc_profile(mpmc_handle h, int enable);
 MPMC_API int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* launches, double* bytes);
 
@@ -310,6 +314,21 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * site-parallel arithmetic in t-sweep form.  Same arithmetic per site as
  * the non-sweep kernel; only the order of the FP64 per-block dot sums
  * differs.  mpmc_get_option returns the mask in effect.
+ * MPMC_OPT_SWEEP_ORDER (default 1): order in which the t-sweep CTAs take the
+ * (2 x 2 x 2 site block, t-segment) pairs: 0 blocks in row order (x fastest)
+ * for each segment in turn; 1 the segments of one block one after another,
+ * the blocks along a Morton curve of the block grid, so that CTAs running at
+ * the same time cover a compact region of the lattice and the neighbour rows
+ * and shared t-planes they read from each other are still in L2.
+ * MPMC_OPT_WAIT_LIMIT: bound of every wait of the t-sweep issue-lean kernels
+ * on their TMA pipeline, in thousands of SM clock cycles (1 .. 4000000;
+ * default 4000000, about 2 s).  A wait that runs out makes the CTA stop
+ * issuing copies, wait (bounded) for the copies it issued and leave; the
+ * call then returns MPMC_ETIMEOUT and the handle stays usable.
+ * MPMC_OPT_TEST_SKIP_COPY (failure-detection test hook, default 0 = off):
+ * value q >= 1 makes every t-sweep CTA leave out the copy of the q-th plane of
+ * its ring, so that the wait for it runs out with nothing in flight into
+ * that buffer.  Not for production use.
  * MPMC_OPT_SWEEP_SEGMENT: t-extent walked by one CTA (0 = automatic, else
  * 1 .. Lt); mpmc_get_option returns the length in effect.  mpmc_autotune
  * sets all four options: block width and the dotted class's kernel from
@@ -323,7 +342,10 @@ enum {
     MPMC_OPT_SWEEP_STENCIL = 2,
     MPMC_OPT_SWEEP_SEGMENT = 3,
     MPMC_OPT_FAST_STENCIL = 4,
-    MPMC_OPT_FAST_SITES = 5
+    MPMC_OPT_FAST_SITES = 5,
+    MPMC_OPT_WAIT_LIMIT = 6,
+    MPMC_OPT_TEST_SKIP_COPY = 7,
+    MPMC_OPT_SWEEP_ORDER = 8
 };
 MPMC_API int mpmc_set_option(mpmc_handle h, int option, int value);
 MPMC_API int mpmc_get_option(mpmc_handle h, int option, int* value);
@@ -373,6 +395,9 @@ MPMC_API int mpmc_deflation_norms(mpmc_handle h, double* d);
  * - sum_i c_i (b_j^H z_i)(u_i^H b_j) with x_j from mpmc_solve and
  * c_i = 1/lambda_i - p_1(lambda_i); mean (1 complex) adds sum_i c_i.  var: the
  * variance of Re s; samples optional (nsamples complex).  FP64 handles only.
+ * p_1 may be the projected composite (Sec. 4.3): then b^H M_1 b with
+ * M_1 b = Z D + p_1(A)(b - (A Z) D), D = H^{-1} U^H b, and c_i = 0 (A^{-1}
+ * and M_1 both map z_i to z_i / lambda_i).
  */
 MPMC_API int mpmc_solve(mpmc_handle h, int pin, const double* B, double* X, int nrhs, double rtol, int m,
                         int maxcycles, int on_device, double* relres, long long* matvecs);
@@ -395,6 +420,32 @@ MPMC_API int mpmc_trace_inverse(mpmc_handle h, int p1, int pin, uint64_t seed, i
  * polynomial), ENOTSUP (projected composite).
  */
 MPMC_API int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace);
+
+/*
+ * mpmc_colouring: a distance-`distance` colouring of the graph of A on the
+ * periodic lattice `dims` (Sec. 3.1: p_3 is chosen of low enough degree for
+ * its trace to be found by probing with a distance colouring of that graph;
+ * Sec. 5, step 3d).  Sites whose hop distance on the periodic lattice is at
+ * most `distance` get different colours, so probing with it is exact for
+ * polynomials of degree <= distance.  colours: V ints (host, caller-owned)
+ * receiving colour(site) in 0 .. *ncolours-1.  Greedy colouring in the
+ * order of a linear colouring of Z^4; host only (no GPU, no handle);
+ * deterministic.  About 110 colours for distance 4 on 24^3 x 32.
+ * Errors: EINVAL (dims < 2, distance < 0, NULL pointer), ENOTSUP (a greedy
+ * pass of more than 8e9 neighbour checks).
+ *
+ * mpmc_trace_probing_colours: the probing estimate of Tr p(A) for polynomial
+ * `index` with any site colouring (colours: V host ints in 0 .. ncolours-1,
+ * copied): the sum over the 12 * ncolours vectors "indicator of the sites of
+ * colour c, component e" of v^H p(A) v, through the same chain kernels and
+ * FP64 fixed-order sums as mpmc_trace_probing.  Exact when same-coloured
+ * sites are more hops apart than the degree of p (e.g. a colouring from
+ * mpmc_colouring with distance >= degree).  Errors: EINVAL (colour out of
+ * range, ncolours < 1), ESTATE, ENOTSUP as mpmc_trace_probing.
+ */
+MPMC_API int mpmc_colouring(const int dims[4], int distance, int* colours, int* ncolours);
+MPMC_API int mpmc_trace_probing_colours(mpmc_handle h, int index, const int* colours, int ncolours,
+                                        double* trace);
 
 /*
  * mpmc_trace_level: one level of mpmc_trace_levels on its own (the same

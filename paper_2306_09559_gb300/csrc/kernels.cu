@@ -95,7 +95,13 @@ __global__ void k_scale(size_t n, const S* __restrict__ in, double sre, double s
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     const cplx<T> sc = {T(sre), T(sim)};
-    st(out + idx * 2, mul(sc, ld(in + idx * 2)));
+    const cplx<T> x = ld(in + idx * 2);
+    cplx<T> r = mul(sc, x);
+    if (sizeof(T) == 4) {   // the scale as an FP32 hi + lo pair (hi is sc)
+        const cplx<T> lo = {T(sre - (double)sc.re), T(sim - (double)sc.im)};
+        r = r + mul(lo, x);
+    }
+    st(out + idx * 2, r);
 }
 
 template <class T>
@@ -361,23 +367,30 @@ __device__ __forceinline__ int probe_colour(int site, int lx, int ly, int lz, in
     return (x % m) + m * ((y % m) + m * ((z % m) + m * (t % m)));
 }
 
+// Colour of a site: from a per-site table (any distance colouring) or, without one,
+// the period-m formula.
+__device__ __forceinline__ int site_colour(const int* tab, int site, int lx, int ly, int lz, int m) {
+    return tab ? __ldg(tab + site) : probe_colour(site, lx, ly, lz, m);
+}
+
 template <class S>
-__global__ void k_probe_block(int V, int lx, int ly, int lz, int m, int q0, int nq, int nb, S* __restrict__ out) {
+__global__ void k_probe_block(int V, int lx, int ly, int lz, int m, const int* __restrict__ tab, int q0, int nq,
+                              int nb, S* __restrict__ out) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (site, e, col)
     if (idx >= (size_t)V * 12 * nb) return;
     const int col = (int)(idx % nb);
     const int e = (int)((idx / nb) % 12);
     const int site = (int)(idx / ((size_t)12 * nb));
     const int q = q0 + col;
-    const bool one = col < nq && e == q % 12 && probe_colour(site, lx, ly, lz, m) == q / 12;
+    const bool one = col < nq && e == q % 12 && site_colour(tab, site, lx, ly, lz, m) == q / 12;
     using T = typename Math<S>::T;
     st(out + idx * 2, cplx<T>{one ? T(1) : T(0), T(0)});
 }
 
 // part[chunk][col] = sum over the chunk's sites of colour c(q) of X[site][e(q)][col] (FP64, site order)
 template <class S>
-__global__ void k_probe_dot(int V, int lx, int ly, int lz, int m, int q0, int nq, int nb, int nchunk,
-                            const S* __restrict__ X, double2* __restrict__ part) {
+__global__ void k_probe_dot(int V, int lx, int ly, int lz, int m, const int* __restrict__ tab, int q0, int nq, int nb,
+                            int nchunk, const S* __restrict__ X, double2* __restrict__ part) {
     const int col = blockIdx.y * blockDim.x + threadIdx.x;
     const int chunk = blockIdx.x;
     if (col >= nb) return;
@@ -387,7 +400,7 @@ __global__ void k_probe_dot(int V, int lx, int ly, int lz, int m, int q0, int nq
         const int per = (V + nchunk - 1) / nchunk;
         const int s1 = min(V, (chunk + 1) * per);
         for (int site = chunk * per; site < s1; ++site) {
-            if (probe_colour(site, lx, ly, lz, m) != c) continue;
+            if (site_colour(tab, site, lx, ly, lz, m) != c) continue;
             const auto v = ld(X + (((size_t)site * 12 + e) * nb + col) * 2);
             sr += (double)v.re;
             si += (double)v.im;
@@ -427,20 +440,28 @@ LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R) {
 
 void fill_floats(StepArgs& a) {
     for (int i = 0; i < 2; ++i) {
-        a.alphaf[i] = (float)a.alpha[i];
-        a.yaf[i] = (float)a.ya[i];
-        a.ybf[i] = (float)a.yb[i];
+        a.alphaf[i] = f32_hi(a.alpha[i]);
+        a.yaf[i] = f32_hi(a.ya[i]);
+        a.ybf[i] = f32_hi(a.yb[i]);
+        a.alphal[i] = f32_lo(a.alpha[i]);
+        a.yal[i] = f32_lo(a.ya[i]);
+        a.ybl[i] = f32_lo(a.yb[i]);
     }
-    a.kappaf = (float)a.kappa;
+    a.kappaf = f32_hi(a.kappa);
+    a.kappal = f32_lo(a.kappa);
 }
 
 void fill_floats(OuterArgs& a) {
     for (int i = 0; i < 2; ++i) {
-        a.alphaf[i] = (float)a.alpha[i];
-        a.betaf[i] = (float)a.beta[i];
-        a.gammaf[i] = (float)a.gamma[i];
+        a.alphaf[i] = f32_hi(a.alpha[i]);
+        a.betaf[i] = f32_hi(a.beta[i]);
+        a.gammaf[i] = f32_hi(a.gamma[i]);
+        a.alphal[i] = f32_lo(a.alpha[i]);
+        a.betal[i] = f32_lo(a.beta[i]);
+        a.gammal[i] = f32_lo(a.gamma[i]);
     }
-    a.kappaf = (float)a.kappa;
+    a.kappaf = f32_hi(a.kappa);
+    a.kappal = f32_lo(a.kappa);
 }
 
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a0,
@@ -574,23 +595,30 @@ void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k,
 
 namespace mpmc {
 
-void launch_probe_block(int storage, const Geom& g, int m, int q0, int nq, int nb, void* out, cudaStream_t s) {
+void launch_probe_block(int storage, const Geom& g, int m, const int* tab, int q0, int nq, int nb, void* out,
+                        cudaStream_t s) {
     const size_t n = (size_t)g.V * 12 * nb;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    if (storage == ST_F64) k_probe_block<double><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (double*)out);
-    else if (storage == ST_F32) k_probe_block<float><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (float*)out);
-    else k_probe_block<__nv_bfloat16><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, (__nv_bfloat16*)out);
+    if (storage == ST_F64)
+        k_probe_block<double><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb, (double*)out);
+    else if (storage == ST_F32)
+        k_probe_block<float><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb, (float*)out);
+    else
+        k_probe_block<__nv_bfloat16><<<blocks, 256, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb,
+                                                           (__nv_bfloat16*)out);
 }
 
-void launch_probe_trace(int storage, const Geom& g, int m, int q0, int nq, int nb, const void* X, int nchunk,
-                        double2* part, double2* total, cudaStream_t s) {
+void launch_probe_trace(int storage, const Geom& g, int m, const int* tab, int q0, int nq, int nb, const void* X,
+                        int nchunk, double2* part, double2* total, cudaStream_t s) {
     const dim3 grid(nchunk, (nb + 63) / 64);
     if (storage == ST_F64)
-        k_probe_dot<double><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk, (const double*)X, part);
+        k_probe_dot<double><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb, nchunk, (const double*)X,
+                                                part);
     else if (storage == ST_F32)
-        k_probe_dot<float><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk, (const float*)X, part);
+        k_probe_dot<float><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb, nchunk, (const float*)X,
+                                               part);
     else
-        k_probe_dot<__nv_bfloat16><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, q0, nq, nb, nchunk,
+        k_probe_dot<__nv_bfloat16><<<grid, 64, 0, s>>>(g.V, g.lx, g.ly, g.lz, m, tab, q0, nq, nb, nchunk,
                                                       (const __nv_bfloat16*)X, part);
     k_probe_sum<<<1, 32, 0, s>>>(nchunk, nb, nq, part, total);
 }

@@ -36,7 +36,10 @@ struct StepArgs {
     double dot_w[2];
     double2* acc;
     double kappa;
-    float alphaf[2], yaf[2], ybf[2], kappaf;   // the same in FP32 (filled by launch_step)
+    // the same in FP32 as hi + lo pairs (filled by launch_step): hi = fl32(c), lo = fl32(c - hi),
+    // so that FP32 kernels apply every coefficient to ~1e-15 relative, not rounded to FP32
+    float alphaf[2], yaf[2], ybf[2], kappaf;
+    float alphal[2], yal[2], ybl[2], kappal;
 };
 
 // Last inner step of a composite outer step (Sec. 3.2):
@@ -53,7 +56,8 @@ struct OuterArgs {
     double dot_w[2];
     double2* acc;
     double kappa;
-    float alphaf[2], betaf[2], gammaf[2], kappaf;
+    float alphaf[2], betaf[2], gammaf[2], kappaf;   // hi parts (as StepArgs)
+    float alphal[2], betal[2], gammal[2], kappal;   // lo parts
 };
 
 struct LaunchCfg {
@@ -72,9 +76,11 @@ void outer_f64(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&
 void outer_f32(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 void outer_bf16(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 
-// FP32 copies of the coefficients (what the FP32 / BF16 kernels use)
+// FP32 hi + lo copies of the coefficients (what the FP32 / BF16 kernels use)
 void fill_floats(StepArgs& a);
 void fill_floats(OuterArgs& a);
+inline float f32_hi(double c) { return (float)c; }
+inline float f32_lo(double c) { return (float)(c - (double)(float)c); }
 
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                  const StepArgs& a, const LaunchCfg& cfg, cudaStream_t s);
@@ -101,9 +107,14 @@ struct FastArgs {
     const float4* Ue;        // expanded links [V][4][9] (re, re, im, im)
     double2* acc;
     double dot_w[2];
-    float alpha[2], beta[2], gamma[2], kappa;
+    float alpha[2], beta[2], gamma[2], kappa;            // hi parts: fl32(c)
+    float alpha_lo[2], beta_lo[2], gamma_lo[2], kappa_lo; // lo parts: fl32(c - hi)
     int lx, ly, lz, lt, V, bc_t, sl;
     unsigned long long mx, my, mz;   // floor(2^64 / extent) + 1
+    const int* blk_order;            // t-sweep: site block of each launch-order index (null: plain order)
+    long long wait_limit;            // t-sweep: bound of each mbarrier wait in SM clock cycles
+    int skip_copy;                   // t-sweep test hook: the q-th plane copy of each CTA (q >= 1) is
+                                     // not issued; 0: none
 };
 bool fast_supported(int storage, int nb);
 int fast_sites_per_cta(int nb);
@@ -113,11 +124,16 @@ void fast_geometry(const Geom& g, FastArgs& a);
 // t-sweep form of the issue-lean kernels (stencil_fsweep.cu): kinds 0, 1,
 // 3, 4; even lx, ly, lz; the input block read by TMA through a tensor map
 // made by fsweep_make_map; accumulator rows cfg.rows.
+// lsm: the variant that stages each plane's links in shared memory with the spinor rows
+// (tile width 16 right-hand sides; its own tensor maps and launch shapes)
 bool fsweep_supported(int storage, const Geom& g, int nb);
-SweepCfg fsweep_config(const Geom& g, int nb, int ts);
-bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb);
+SweepCfg fsweep_config(const Geom& g, int nb, int ts, bool lsm);
+// Launch order of the (lx/2)(ly/2)(lz/2) site blocks along a Morton (Z-order) curve of the
+// block grid, so that CTAs running at the same time cover compact regions of the lattice
+void fsweep_morton_order(const Geom& g, int* order);
+bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, bool lsm);
 int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepCfg& c, const void* map, int* err,
-                  cudaStream_t s);
+                  cudaStream_t s, bool lsm);
 // Z4 words of a noise block: words[site][col] = Philox word 0 of (j0 + col, site, level)
 void launch_noise_words(const Geom& g, int nb, const NoiseSpec& ns, uint32_t* words, cudaStream_t s);
 // expanded links (re, re, im, im) in float from complex-double [mu][site][3][3]
@@ -214,12 +230,14 @@ void launch_normalize(size_t n, const double2* w, const double* nrm2, double2* d
 void launch_combine(size_t n, int m, const double2* Vb, const double2* Y, int k, double2* Z, cudaStream_t s);
 // complex double [site][e][1] <-> storage conversions for a single vector are import/export with nb = 1
 
-// Probing (period-m distance colouring): out = probe block of columns q0 .. q0+nq-1
-// (zero beyond nq); total += sum of X over the probe entries of those columns (FP64,
-// fixed order; part: nchunk x nb scratch)
-void launch_probe_block(int storage, const Geom& g, int m, int q0, int nq, int nb, void* out, cudaStream_t s);
-void launch_probe_trace(int storage, const Geom& g, int m, int q0, int nq, int nb, const void* X, int nchunk,
-                        double2* part, double2* total, cudaStream_t s);
+// Probing: out = probe block of columns q0 .. q0+nq-1 (zero beyond nq); total += sum of X
+// over the probe entries of those columns (FP64, fixed order; part: nchunk x nb scratch).
+// Site colours from the device table tab (V entries), or with tab == nullptr from the
+// period-m colouring x%m + m (y%m) + m^2 (z%m) + m^3 (t%m).
+void launch_probe_block(int storage, const Geom& g, int m, const int* tab, int q0, int nq, int nb, void* out,
+                        cudaStream_t s);
+void launch_probe_trace(int storage, const Geom& g, int m, const int* tab, int q0, int nq, int nb, const void* X,
+                        int nchunk, double2* part, double2* total, cudaStream_t s);
 
 int mdot_parts(size_t n);
 

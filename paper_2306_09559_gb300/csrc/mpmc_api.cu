@@ -112,6 +112,10 @@ struct mpmc_ctx {
     int sweep_ts = 0;
     int use_fast = 7;             // issue-lean kernels per class (FP32 / BF16S, block widths 16 .. 1024)
     int fast_sl = 1;              // sites per thread of the issue-lean kernels
+    long long wait_limit = 4000000000LL;   // bound of each t-sweep mbarrier wait (SM clock cycles, ~2 s)
+    int skip_copy = 0;            // failure-detection test hook: t-sweep plane copy left out (0: none)
+    int sweep_order = 1;          // launch order of the t-sweep site blocks: 0 plain, 1 Morton curve
+    int* blk_order = nullptr;     // device table of that order (made with the first t-sweep shape)
     std::vector<SweepMap> maps;
     // work
     int nb_user = 0;
@@ -128,6 +132,8 @@ struct mpmc_ctx {
     long long launches = 0;
     double2* probe = nullptr;     // probing: [nchunk][nb] partial sums + 1 total
     size_t probe_cap = 0;
+    int* probe_tab = nullptr;     // probing: site colours of the caller's colouring
+    size_t probe_tab_cap = 0;
     double2* sol = nullptr;       // solver: basis (m+1 vectors) and 4 work vectors + coefficients
     size_t sol_cap = 0;
     unsigned long long gen = 0;   // bumped by every call that changes what a trace launches
@@ -136,10 +142,11 @@ struct mpmc_ctx {
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     std::vector<int> ev_cls;
+    std::vector<int> ev_var;      // kernel of a stencil launch (PROF_K_*), -1 for other classes
     std::vector<double> ev_bytes;
-    double prof_ms[3] = {0, 0, 0};
-    long long prof_n[3] = {0, 0, 0};
-    double prof_b[3] = {0, 0, 0};
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::string err;
 };
 
@@ -217,7 +224,13 @@ int set_cfg(mpmc_ctx* h, Workspace& w) {
         w.fast_gx = (h->g.V + per - 1) / per;
     }
     w.fsweep = w.fast && (h->use_sweep & h->use_fast & 7) && fsweep_supported(w.storage, h->g, w.nb);
-    if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts);
+    if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts, (h->use_sweep & 16) != 0);
+    if (w.fsweep && !h->blk_order) {
+        std::vector<int> order((size_t)w.fsw.nblk);
+        fsweep_morton_order(h->g, order.data());
+        if (int rc = dev_alloc(h, &h->blk_order, sizeof(int) * order.size())) return rc;
+        CK(cudaMemcpy(h->blk_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+    }
     w.sweep = (h->use_sweep & 8) && sweep_supported(w.storage, h->g, w.nb);
     if (w.sweep) w.sw = sweep_config(h->g, w.nb, h->sweep_ts);
     // one accumulator row per site block (k_step) or per site block and t-segment (sweep)
@@ -271,6 +284,7 @@ int prof_begin(mpmc_ctx* h, int cls, double bytes) {
     }
     CK(cudaEventRecord(h->ev[h->ev_used], h->stream));
     h->ev_cls.push_back(cls);
+    h->ev_var.push_back(-1);
     h->ev_bytes.push_back(bytes);
     return MPMC_OK;
 }
@@ -287,17 +301,26 @@ int prof_collect(mpmc_ctx* h) {
     for (size_t i = 0; i < h->ev_cls.size(); ++i) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]));
-        h->prof_ms[h->ev_cls[i]] += ms;
-        h->prof_n[h->ev_cls[i]] += 1;
-        h->prof_b[h->ev_cls[i]] += h->ev_bytes[i];
+        for (int c : {h->ev_cls[i], h->ev_var[i]}) {
+            if (c < 0) continue;
+            h->prof_ms[c] += ms;
+            h->prof_n[c] += 1;
+            h->prof_b[c] += h->ev_bytes[i];
+        }
     }
     h->ev_cls.clear();
+    h->ev_var.clear();
     h->ev_bytes.clear();
     h->ev_used = 0;
     return MPMC_OK;
 }
 
 enum { PROF_STENCIL = 0, PROF_DEFLATION = 1, PROF_OTHER = 2 };
+// stencil launches by kernel: t-sweep issue-lean, issue-lean, site-parallel, t-sweep site-parallel
+enum { PROF_K_FSWEEP = 3, PROF_K_FAST = 4, PROF_K_SITE = 5, PROF_K_SWEEP = 6 };
+void prof_variant(mpmc_ctx* h, int var) {
+    if (h->prof && !h->ev_var.empty()) h->ev_var.back() = var;
+}
 
 double link_bytes(const mpmc_ctx* h, int st) { return (double)h->g.V * 36 * (st == ST_F64 ? 16 : 8); }
 
@@ -318,7 +341,7 @@ const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in, int kind
     for (const SweepMap& m : h->maps)
         if (m.p == in && m.storage == ws.storage && m.nb == ws.nb && m.V == h->g.V && m.kind == kind) return m.m;
     SweepMap m;
-    const bool made = kind ? fsweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb)
+    const bool made = kind ? fsweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb, kind == 2)
                            : sweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb);
     if (!made) return nullptr;
     m.p = in;
@@ -348,7 +371,11 @@ FastArgs fast_args(const mpmc_ctx* h, const Workspace& ws, double kappa) {
     f.Ue = h->links_ex;
     f.words = ws.words;
     f.sl = h->fast_sl;
-    f.kappa = (float)kappa;
+    f.wait_limit = h->wait_limit;
+    f.blk_order = h->sweep_order ? h->blk_order : nullptr;
+    f.skip_copy = h->skip_copy;
+    f.kappa = f32_hi(kappa);
+    f.kappa_lo = f32_lo(kappa);
     return f;
 }
 
@@ -367,11 +394,16 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         f.acc = a.acc;
         f.dot_w[0] = a.dot_w[0];
         f.dot_w[1] = a.dot_w[1];
-        f.alpha[0] = (float)a.alpha[0];
-        f.alpha[1] = (float)a.alpha[1];
-        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, 1) : nullptr;
+        for (int i = 0; i < 2; ++i) {
+            f.alpha[i] = f32_hi(a.alpha[i]);
+            f.alpha_lo[i] = f32_lo(a.alpha[i]);
+        }
+        const bool lsm = (h->use_sweep & 16) != 0;
+        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, lsm ? 2 : 1)
+                                                                            : nullptr;
+        prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
-            if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream))
+            if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream, lsm))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep step launch failed");
         } else if (launch_fast(ws.storage, ws.nb, kind, f, ws.fast_gx, h->stream)) {
             return fail(h, MPMC_ECUDA, "issue-lean step launch failed");
@@ -379,6 +411,7 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         return MPMC_OK;
     }
     const void* map = (ws.sweep && a.in) ? sweep_map(h, ws, a.in, 0) : nullptr;
+    prof_variant(h, map ? PROF_K_SWEEP : PROF_K_SITE);
     if (map) {
         if (launch_sweep_step(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, a, ws.sw, map, h->d_err,
                               h->stream))
@@ -413,13 +446,18 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
         f.dot_w[0] = o.dot_w[0];
         f.dot_w[1] = o.dot_w[1];
         for (int i = 0; i < 2; ++i) {
-            f.alpha[i] = (float)o.alpha[i];
-            f.beta[i] = (float)o.beta[i];
-            f.gamma[i] = (float)o.gamma[i];
+            f.alpha[i] = f32_hi(o.alpha[i]);
+            f.beta[i] = f32_hi(o.beta[i]);
+            f.gamma[i] = f32_hi(o.gamma[i]);
+            f.alpha_lo[i] = f32_lo(o.alpha[i]);
+            f.beta_lo[i] = f32_lo(o.beta[i]);
+            f.gamma_lo[i] = f32_lo(o.gamma[i]);
         }
-        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, 1) : nullptr;
+        const bool lsm = (h->use_sweep & 16) != 0;
+        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, lsm ? 2 : 1) : nullptr;
+        prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
-            if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream))
+            if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream, lsm))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep outer launch failed");
         } else if (launch_fast(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fast_gx, h->stream)) {
             return fail(h, MPMC_ECUDA, "issue-lean outer launch failed");
@@ -427,6 +465,7 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
         return MPMC_OK;
     }
     const void* map = ws.sweep ? sweep_map(h, ws, o.in, 0) : nullptr;
+    prof_variant(h, map ? PROF_K_SWEEP : PROF_K_SITE);
     if (map) {
         if (launch_sweep_outer(ws.storage, h->g, links_for(h, ws.storage), ws.nb, ns, o, ws.sw, map, h->d_err,
                                h->stream))
@@ -508,15 +547,15 @@ int num_levels(const mpmc_ctx* h) {
 
 inline void setc(double (&d)[2], cd z) { d[0] = z.real(); d[1] = z.imag(); }
 
-// A coefficient as the kernels of a storage format apply it: reduced-precision
-// kernels use the FP32 value, so the host uses the same value wherever it
-// weights their results (dot weights, closed-form terms).  The chain then
-// applies exactly the polynomial with roots 1/rnd(1/theta) to the matrix with
-// kappa rounded once.
-inline cd rnd(int storage, cd z) {
-    if (storage == ST_F64) return z;
-    return cd((double)(float)z.real(), (double)(float)z.imag());
-}
+// A coefficient as the kernels of a storage format apply it.  Reduced-precision
+// kernels take every coefficient (kappa, 1/theta, 1/eta, scales) as an FP32
+// hi + lo pair and apply both parts, so they use the FP64 value to ~1e-15 and
+// the chain applies the same matrix and polynomial as the FP64 path: rounding
+// a coefficient to FP32 would shift the matrix or a root by ~6e-8 for every
+// vector alike, a systematic change of the traces that no number of noise
+// vectors averages out.  The host therefore weights their results with the
+// FP64 values themselves.
+inline cd rnd(int, cd z) { return z; }
 
 // ------------------------------------------------------------------ chains
 // Trace mode: acc += sum of weighted b^H w over all steps of p(A) applied to
@@ -1040,6 +1079,8 @@ int mpmc_destroy(mpmc_handle h) {
     dev_free(h->links32);
     dev_free(h->links_ex);
     dev_free(h->probe);
+    dev_free(h->probe_tab);
+    dev_free(h->blk_order);
     dev_free(h->sol);
     dev_free(h->samples);
     dev_free(h->io);
@@ -1181,15 +1222,19 @@ static int set_deflation_impl(mpmc_handle h, const double* Z, const double* lamb
     return upload_coefficients(h);
 }
 
-int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
-    if (!h) return MPMC_EINVAL;
-    if (!trace || m < 1 || h->g.lx % m || h->g.ly % m || h->g.lz % m || h->g.lt % m)
-        return fail(h, MPMC_EINVAL, "the period m must divide every lattice extent");
+}  // extern "C"
+
+namespace {
+
+// Sum of v^H p(A) v over the 12 * ncolours probe vectors of a colouring: from the device
+// table tab (V entries) or, with tab == nullptr, the period-m colouring.
+int probing_sum(mpmc_ctx* h, int index, int m, const int* tab, long long ncolours, double* trace) {
+    if (!trace) return fail(h, MPMC_EINVAL, "trace is NULL");
     if (index < 0 || index >= MPMC_MAX_POLYS) return fail(h, MPMC_EINVAL, "polynomial index out of range");
     const PolyDef& p = h->polys[index];
     if (!p.set) return fail(h, MPMC_ESTATE, "polynomial not set");
     if (p.kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "probing of the projected composite");
-    const long long nq_all = 12LL * m * m * m * m;
+    const long long nq_all = 12LL * ncolours;
     const int nb = (int)std::min<long long>(default_nb(h), nq_all);
     if (int rc = ensure_ws(h, h->ws, h->storage, nb)) return rc;
     const int nchunk = 152;
@@ -1205,10 +1250,10 @@ int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
     Workspace& ws = h->ws;
     for (long long q0 = 0; q0 < nq_all; q0 += nb) {
         const int cnt = (int)std::min<long long>(nb, nq_all - q0);
-        launch_probe_block(ws.storage, h->g, m, (int)q0, cnt, nb, ws.r, h->stream);
+        launch_probe_block(ws.storage, h->g, m, tab, (int)q0, cnt, nb, ws.r, h->stream);
         LAUNCHED(1);
         if (int rc = chain_apply(h, ws, p, ws.r, ws.x)) return rc;
-        launch_probe_trace(ws.storage, h->g, m, (int)q0, cnt, nb, ws.x, nchunk, h->probe, total, h->stream);
+        launch_probe_trace(ws.storage, h->g, m, tab, (int)q0, cnt, nb, ws.x, nchunk, h->probe, total, h->stream);
         LAUNCHED(2);
     }
     double2 t;
@@ -1218,6 +1263,33 @@ int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
     trace[0] = t.x;
     trace[1] = t.y;
     return prof_collect(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace) {
+    if (!h) return MPMC_EINVAL;
+    if (m < 1 || h->g.lx % m || h->g.ly % m || h->g.lz % m || h->g.lt % m)
+        return fail(h, MPMC_EINVAL, "the period m must divide every lattice extent");
+    return probing_sum(h, index, m, nullptr, 1LL * m * m * m * m, trace);
+}
+
+int mpmc_trace_probing_colours(mpmc_handle h, int index, const int* colours, int ncolours, double* trace) {
+    if (!h) return MPMC_EINVAL;
+    if (!colours || ncolours < 1 || ncolours > h->g.V) return fail(h, MPMC_EINVAL, "bad colouring");
+    for (int s = 0; s < h->g.V; ++s)
+        if (colours[s] < 0 || colours[s] >= ncolours) return fail(h, MPMC_EINVAL, "a site colour is out of range");
+    if ((size_t)h->g.V > h->probe_tab_cap) {
+        dev_free(h->probe_tab);
+    dev_free(h->blk_order);
+        h->probe_tab_cap = 0;
+        if (int rc = dev_alloc(h, &h->probe_tab, sizeof(int) * (size_t)h->g.V)) return rc;
+        h->probe_tab_cap = h->g.V;
+    }
+    CK(cudaMemcpyAsync(h->probe_tab, colours, sizeof(int) * (size_t)h->g.V, cudaMemcpyHostToDevice, h->stream));
+    return probing_sum(h, index, 1, h->probe_tab, ncolours, trace);
 }
 
 // ------------------------------------------------------------------ linear equations
@@ -1431,7 +1503,8 @@ int mpmc_trace_inverse(mpmc_handle h, int p1, int pin, uint64_t seed, int nsampl
     if (!h) return MPMC_EINVAL;
     if (nsamples < 1 || first < 0 || !(rtol > 0)) return fail(h, MPMC_EINVAL, "bad trace_inverse arguments");
     if (p1 < 0 || p1 >= MPMC_MAX_POLYS || !h->polys[p1].set) return fail(h, MPMC_ESTATE, "p_1 not set");
-    if (h->polys[p1].kind == MPMC_DEFLATED_COMPOSITE) return fail(h, MPMC_ENOTSUP, "p_1 must not be projected");
+    const bool proj = h->polys[p1].kind == MPMC_DEFLATED_COMPOSITE;
+    if (proj && h->k == 0) return fail(h, MPMC_ESTATE, "the projected composite needs deflation vectors");
     if (int rc = solve_setup(h, pin, m)) return rc;
     const size_t n = nsites12(h);
     const int k = h->k;
@@ -1461,14 +1534,30 @@ int mpmc_trace_inverse(mpmc_handle h, int p1, int pin, uint64_t seed, int nsampl
         CK(cudaMemcpyAsync(&dot, h->kr_h, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         cd sample(dot.x, dot.y);
-        // b^H p_1(A) b
-        if (int rc = chain_apply(h, ws, h->polys[p1], b, pb)) return rc;
+        // b^H p_1(A) b;  projected p_1 (Sec. 4.3): M_1 b = Z D + p_1(A)(b - (A Z) D), D = H^{-1} U^H b
+        if (proj) {
+            double2* r = h->sol + (size_t)(m + 1) * n;      // the solver's residual: free between solves
+            const int nsplit = gram_nsplit(h->g.V);
+            if (int rc = ensure_gram_part(h, (size_t)nsplit * k)) return rc;
+            launch_block_gram(ST_F64, h->g.V, h->Zb, k, ST_F64, b, 1, 1, h->gram_part, nsplit, h->G2, h->stream);
+            launch_proj_coef(k, 1, h->d_pair, h->d_invd, h->d_Hinv, nullptr, h->G2, h->D, h->D32, nullptr,
+                             h->stream);
+            launch_rank_update(ST_F64, ST_F64, h->g.V, 1, h->Wb, k, h->D, h->D32, -1.0, b, NoiseSpec{0, 0, 0}, r,
+                               h->stream);
+            LAUNCHED(4);
+            if (int rc = chain_apply(h, ws, h->polys[p1], r, pb)) return rc;
+            launch_rank_update(ST_F64, ST_F64, h->g.V, 1, h->Zb, k, h->D, h->D32, 1.0, pb, NoiseSpec{0, 0, 0}, pb,
+                               h->stream);
+            LAUNCHED(1);
+        } else if (int rc = chain_apply(h, ws, h->polys[p1], b, pb)) {
+            return rc;
+        }
         launch_mdot(n, 1, b, pb, h->kr_part, h->kr_h, h->stream);
         CK(cudaMemcpyAsync(&dot, h->kr_h, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
         LAUNCHED(2);
         CK(cudaStreamSynchronize(h->stream));
         sample -= cd(dot.x, dot.y);
-        if (k > 0) {
+        if (k > 0 && !proj) {
             // sum_i c_i (b^H z_i)(u_i^H b), u_i = gamma5 z_pair(i) / conj(d_i)
             const int nsplit = gram_nsplit(h->g.V);
             if (int rc = ensure_gram_part(h, (size_t)nsplit * k)) return rc;
@@ -1877,7 +1966,7 @@ int mpmc_profile(mpmc_handle h, int enable) {
     CK(cudaStreamSynchronize(h->stream));
     if (int rc = prof_collect(h)) return rc;
     if (enable) {
-        for (int c = 0; c < 3; ++c) { h->prof_ms[c] = 0; h->prof_n[c] = 0; h->prof_b[c] = 0; }
+        for (int c = 0; c < 8; ++c) { h->prof_ms[c] = 0; h->prof_n[c] = 0; h->prof_b[c] = 0; }
     }
     h->prof = enable != 0;
     return MPMC_OK;
@@ -1885,7 +1974,7 @@ int mpmc_profile(mpmc_handle h, int enable) {
 
 int mpmc_profile_read(mpmc_handle h, int cls, double* ms, long long* launches, double* bytes) {
     if (!h) return MPMC_EINVAL;
-    if (cls < 0 || cls > 2) return fail(h, MPMC_EINVAL, "profile class out of range");
+    if (cls < 0 || cls > 6) return fail(h, MPMC_EINVAL, "profile class out of range");
     CK(cudaStreamSynchronize(h->stream));
     if (int rc = prof_collect(h)) return rc;
     if (ms) *ms = h->prof_ms[cls];
@@ -2146,7 +2235,7 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->use_tc = value != 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            if (value < 0 || value > 15) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 15");
+            if (value < 0 || value > 31) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 31");
             h->use_sweep = value;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
@@ -2160,6 +2249,18 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
         case MPMC_OPT_FAST_SITES:
             if (value < 1 || value > 16) return fail(h, MPMC_EINVAL, "sites per thread out of range");
             h->fast_sl = value;
+            return MPMC_OK;
+        case MPMC_OPT_WAIT_LIMIT:
+            if (value < 1 || value > 4000000) return fail(h, MPMC_EINVAL, "wait limit out of range (1 .. 4000000)");
+            h->wait_limit = 1000LL * value;
+            return MPMC_OK;
+        case MPMC_OPT_TEST_SKIP_COPY:
+            if (value < 0) return fail(h, MPMC_EINVAL, "skip-copy index must be >= 0");
+            h->skip_copy = value;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_ORDER:
+            if (value < 0 || value > 1) return fail(h, MPMC_EINVAL, "sweep order is 0 (plain) or 1 (Morton)");
+            h->sweep_order = value;
             return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");
@@ -2181,12 +2282,13 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
             if (fast_supported(h->storage, cur_nb(h)) && fsweep_supported(h->storage, h->g, cur_nb(h)))
                 v |= h->use_sweep & h->use_fast & 7;
             if (sweep_supported(h->storage, h->g, cur_nb(h))) v |= h->use_sweep & 8;
+            if (v & 7) v |= h->use_sweep & 16;
             *value = v;
             return MPMC_OK;
         }
         case MPMC_OPT_SWEEP_SEGMENT:
             *value = ((h->use_fast & 7) && fsweep_supported(h->storage, h->g, cur_nb(h)))
-                         ? fsweep_config(h->g, cur_nb(h), h->sweep_ts).ts
+                         ? fsweep_config(h->g, cur_nb(h), h->sweep_ts, (h->use_sweep & 16) != 0).ts
                          : sweep_config(h->g, cur_nb(h), h->sweep_ts).ts;
             return MPMC_OK;
         case MPMC_OPT_FAST_STENCIL:
@@ -2194,6 +2296,15 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
             return MPMC_OK;
         case MPMC_OPT_FAST_SITES:
             *value = h->fast_sl;
+            return MPMC_OK;
+        case MPMC_OPT_WAIT_LIMIT:
+            *value = (int)(h->wait_limit / 1000);
+            return MPMC_OK;
+        case MPMC_OPT_TEST_SKIP_COPY:
+            *value = h->skip_copy;
+            return MPMC_OK;
+        case MPMC_OPT_SWEEP_ORDER:
+            *value = h->sweep_order;
             return MPMC_OK;
         default:
             return fail(h, MPMC_EINVAL, "unknown option");

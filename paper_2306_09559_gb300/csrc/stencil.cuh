@@ -225,27 +225,47 @@ __device__ __forceinline__ void hopping_r(const Lattice& L, const T* __restrict_
     src.get(nb.bwd[3], col0, psi); load_link(U, nb.bwd[3], 3, u); hop_r<3, false, true>(psi, u, sb, acc);
 }
 
+// A coefficient c as the kernels of one arithmetic apply it: FP64 kernels use c;
+// FP32 kernels use the pair hi = fl32(c), lo = fl32(c - hi) and apply both, so the
+// coefficient enters to ~1e-15 relative and FP32 chains apply the same matrix and
+// polynomial as FP64 ones (only the arithmetic rounds, not the coefficients).
 template <class T> struct Coef;
 template <> struct Coef<float> {
+    static constexpr bool split = true;
     static __device__ __forceinline__ cplx<float> get(const double (&)[2], const float (&f)[2]) { return {f[0], f[1]}; }
     static __device__ __forceinline__ float real(double, float f) { return f; }
 };
 template <> struct Coef<double> {
+    static constexpr bool split = false;
     static __device__ __forceinline__ cplx<double> get(const double (&d)[2], const float (&)[2]) { return {d[0], d[1]}; }
     static __device__ __forceinline__ double real(double d, float) { return d; }
 };
 
-// t = own - kappa * hw  (A applied), then out = own - alpha * t
-template <class T>
-__device__ __forceinline__ cplx<T> apply_A_elem(cplx<T> own, cplx<T> hw, T kappa) {
-    return {fma(-kappa, hw.re, own.re), fma(-kappa, hw.im, own.im)};
+// t = own - kappa * hw  (A applied): kappa = kh (+ kl when SPLIT)
+template <bool SPLIT, class T>
+__device__ __forceinline__ cplx<T> apply_A_elem(cplx<T> own, cplx<T> hw, T kh, T kl) {
+    cplx<T> t{fma(-kh, hw.re, own.re), fma(-kh, hw.im, own.im)};
+    if (SPLIT) {
+        t.re = fma(-kl, hw.re, t.re);
+        t.im = fma(-kl, hw.im, t.im);
+    }
+    return t;
 }
-template <class T>
-__device__ __forceinline__ cplx<T> minus_alpha(cplx<T> own, cplx<T> alpha, cplx<T> t) {
+// own - alpha * t: alpha = ah (+ al when SPLIT)
+template <bool SPLIT, class T>
+__device__ __forceinline__ cplx<T> minus_alpha(cplx<T> own, cplx<T> ah, cplx<T> al, cplx<T> t) {
     cplx<T> o = own;
-    cmac(o, cplx<T>{-alpha.re, -alpha.im}, t);
+    cmac(o, cplx<T>{-ah.re, -ah.im}, t);
+    if (SPLIT) cmac(o, cplx<T>{-al.re, -al.im}, t);
     return o;
 }
+// acc += c * v: c = ch (+ cl when SPLIT)
+template <bool SPLIT, class T>
+__device__ __forceinline__ void cmac2(cplx<T>& acc, cplx<T> ch, cplx<T> cl, cplx<T> v) {
+    cmac(acc, ch, v);
+    if (SPLIT) cmac(acc, cl, v);
+}
+template <class T> __device__ __forceinline__ cplx<T> lo_of(const float (&l)[2]) { return {T(l[0]), T(l[1])}; }
 
 // Reduce R per-thread partial dots over threadIdx.y in fixed order (FP64),
 // then acc[blockIdx.x][col] += w * sum.
@@ -280,12 +300,14 @@ template <class S, int R, bool NOISE_IN, bool DOT, int YMODE>
 __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
                                               int nb, NoiseKey nk, int sl) {
     using T = typename Math<S>::T;
+    constexpr bool SP = Coef<T>::split;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
     const bool op_only = a.op_only;
     const cplx<T> cya = Coef<T>::get(a.ya, a.yaf), cyb = Coef<T>::get(a.yb, a.ybf);
+    const cplx<T> cyal = lo_of<T>(a.yal), cybl = lo_of<T>(a.ybl);
     cplx<T> dsum[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dsum[r] = cz<T>();
@@ -315,8 +337,8 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typen
             cplx<T> out[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const cplx<T> t = apply_A_elem(own[e][r], hw[e][r], kap);
-                out[r] = op_only ? t : minus_alpha(own[e][r], cal, t);
+                const cplx<T> t = apply_A_elem<SP>(own[e][r], hw[e][r], kap, kapl);
+                out[r] = op_only ? t : minus_alpha<SP>(own[e][r], cal, call, t);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), out[r]);
             }
             VecIO<S, R>::st(po + (size_t)e * nb * 2, out);
@@ -325,14 +347,15 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typen
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     yv[r] = cmul_f(cya, own[e][r]);
-                    cmac(yv[r], cyb, out[r]);
+                    if (SP) cmac(yv[r], cyal, own[e][r]);
+                    cmac2<SP>(yv[r], cyb, cybl, out[r]);
                 }
                 VecIO<S, R>::st(py + (size_t)e * nb * 2, yv);
             } else if (YMODE == 2) {
                 cplx<T> yv[R];
                 VecIO<S, R>::ld(py + (size_t)e * nb * 2, yv);
 #pragma unroll
-                for (int r = 0; r < R; ++r) cmac(yv[r], cyb, out[r]);
+                for (int r = 0; r < R; ++r) cmac2<SP>(yv[r], cyb, cybl, out[r]);
                 VecIO<S, R>::st(py + (size_t)e * nb * 2, yv);
             }
         }
@@ -345,11 +368,13 @@ template <class S, int R, bool DOT>
 __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
                                                int nb, NoiseKey nk, int sl) {
     using T = typename Math<S>::T;
+    constexpr bool SP = Coef<T>::split;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
     const cplx<T> cb = Coef<T>::get(a.beta, a.betaf), cg = Coef<T>::get(a.gamma, a.gammaf);
+    const cplx<T> cbl = lo_of<T>(a.betal), cgl = lo_of<T>(a.gammal);
     cplx<T> dsum[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dsum[r] = cz<T>();
@@ -376,10 +401,10 @@ __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typ
             VecIO<S, R>::ld(py + (size_t)e * nb * 2, yv);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const cplx<T> t = minus_alpha(own[e][r], cal, apply_A_elem(own[e][r], hw[e][r], kap));
-                const cplx<T> wn = minus_alpha(wv[r], cb, wv[r] - t);
+                const cplx<T> t = minus_alpha<SP>(own[e][r], cal, call, apply_A_elem<SP>(own[e][r], hw[e][r], kap, kapl));
+                const cplx<T> wn = minus_alpha<SP>(wv[r], cb, cbl, wv[r] - t);
                 wv[r] = wn;
-                cmac(yv[r], cg, wn);
+                cmac2<SP>(yv[r], cg, cgl, wn);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), yv[r]);
             }
             VecIO<S, R>::st(pwo + (size_t)e * nb * 2, wv);

@@ -73,7 +73,13 @@ template <int NB> struct NoiseRow {
 // expanded link, reconstruction.  up[3*spin + c] for spins 0, 1; lower
 // spins: lr (real coefficients) and lj (coefficients of i), index
 // 3*(spin-2) + c.  sgn (applied when use_sgn) is the boundary sign.
-template <int MU, bool FWD>
+// A link element: read-only global load, or (SMEM) a plain load of a copy staged in shared memory
+template <bool SMEM> __device__ __forceinline__ float4 ld_link(const float4* p) {
+    if constexpr (SMEM) return *p;
+    else return __ldg(p);
+}
+
+template <int MU, bool FWD, bool SMEM = false>
 __device__ __forceinline__ void hop_p(const float2 (&p)[12], const float4* __restrict__ L, float sgn, bool use_sgn,
                                       float2 (&up)[6], float2 (&lr)[6], float2 (&lj)[6]) {
     float2 h0[3], h1[3], i0[3], i1[3];
@@ -109,7 +115,7 @@ __device__ __forceinline__ void hop_p(const float2 (&p)[12], const float4* __res
         float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float4 u = __ldg(L + (FWD ? 3 * r + c : 3 * c + r));
+            const float4 u = ld_link<SMEM>(L + (FWD ? 3 * r + c : 3 * c + r));
             const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
             g0 = fma2(ur, h0[c], g0);
             g0 = fma2(ui, i0[c], g0);
@@ -191,6 +197,17 @@ __device__ __forceinline__ float2 cmac2(float2 acc, float2 c, float2 v) {
     acc.y = fmaf(c.y, v.x, acc.y);
     return acc;
 }
+// The same with a coefficient given as an FP32 hi + lo pair (applied to ~1e-15 relative):
+// t = own - kappa hw;  own - alpha t;  acc + c v
+__device__ __forceinline__ float2 apply_A2(float2 own, float2 hw, float2 mkh, float2 mkl) {
+    return fma2(mkl, hw, fma2(mkh, hw, own));
+}
+__device__ __forceinline__ float2 minus_alpha2(float2 own, float2 ah, float2 al, float2 t) {
+    return minus_alpha2(minus_alpha2(own, ah, t), al, t);
+}
+__device__ __forceinline__ float2 cmac2(float2 acc, float2 ch, float2 cl, float2 v) {
+    return cmac2(cmac2(acc, ch, v), cl, v);
+}
 
 // (cr, cr, ci, ci) of conj(i^q) and i^q, for the shared tables
 __device__ __forceinline__ float4 z4_conj_entry(int q) {
@@ -216,8 +233,8 @@ __global__ void __launch_bounds__(256) k_fast(const FastArgs a) {
     __syncthreads();
     const int col = blockIdx.y * TW + threadIdx.x;
     float dre = 0.f, dim = 0.f;
-    const float2 al = make_float2(a.alpha[0], a.alpha[1]);
-    const float2 mk = make_float2(-a.kappa, -a.kappa);
+    const float2 al = make_float2(a.alpha[0], a.alpha[1]), all = make_float2(a.alpha_lo[0], a.alpha_lo[1]);
+    const float2 mk = make_float2(-a.kappa, -a.kappa), mkl = make_float2(-a.kappa_lo, -a.kappa_lo);
     for (int it = 0; it < a.sl; ++it) {
         const int site = (blockIdx.x * a.sl + it) * SB + threadIdx.y;
         if (site >= a.V) break;
@@ -237,18 +254,19 @@ __global__ void __launch_bounds__(256) k_fast(const FastArgs a) {
 #pragma unroll
         for (int e = 0; e < 12; ++e) {
             const float2 own = NOISE ? zval[(word >> (2 * e)) & 3u] : Row<S>::ld(pin + (size_t)e * NB * 2);
-            const float2 t = fma2(mk, hw[e], own);                 // own - kappa H own
+            const float2 t = apply_A2(own, hw[e], mk, mkl);        // own - kappa H own
             float2 v;
             if (!OUTER) {
-                v = minus_alpha2(own, al, t);                      // (I - A/theta) own
+                v = minus_alpha2(own, al, all, t);                 // (I - A/theta) own
                 Row<S>::st(reinterpret_cast<S*>(a.out) + off + (size_t)e * NB * 2, v);
             } else {
-                const float2 tt = minus_alpha2(own, al, t);        // pi_in(A) w
+                const float2 tt = minus_alpha2(own, al, all, t);   // pi_in(A) w
                 const size_t oe = off + (size_t)e * NB * 2;
                 const float2 wv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.w) + oe);
                 float2 yv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.y) + oe);
-                const float2 wn = minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]), sub2(wv, tt));
-                yv = cmac2(yv, make_float2(a.gamma[0], a.gamma[1]), wn);
+                const float2 wn = minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]),
+                                               make_float2(a.beta_lo[0], a.beta_lo[1]), sub2(wv, tt));
+                yv = cmac2(yv, make_float2(a.gamma[0], a.gamma[1]), make_float2(a.gamma_lo[0], a.gamma_lo[1]), wn);
                 Row<S>::st(reinterpret_cast<S*>(a.out) + oe, wn);
                 Row<S>::st(reinterpret_cast<S*>(a.y) + oe, yv);
                 v = yv;

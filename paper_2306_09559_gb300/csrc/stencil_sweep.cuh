@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
     if (threadIdx.x == 0)
         for (int rel = 0; rel < SWEEP_RING && rel < nrel; ++rel) issue(rel);
 
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf);
+    constexpr bool SP = Coef<T>::split;
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
     const long long deadline = clock64() + SWEEP_TIMEOUT;
     double dre = 0.0, dim = 0.0;
 
@@ -148,29 +149,32 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
             cplx<T> dsum = cz<T>();
             if constexpr (!OUTER) {
                 const cplx<T> cya = Coef<T>::get(a.ya, a.yaf), cyb = Coef<T>::get(a.yb, a.ybf);
+                const cplx<T> cyal = lo_of<T>(a.yal), cybl = lo_of<T>(a.ybl);
                 S* po = reinterpret_cast<S*>(a.out) + off;
                 S* py = reinterpret_cast<S*>(a.y) + off;
 #pragma unroll
                 for (int e = 0; e < 12; ++e) {
                     cplx<T> out[1];
-                    const cplx<T> tt = apply_A_elem(own[e][0], acc[e][0], kap);
-                    out[0] = a.op_only ? tt : minus_alpha(own[e][0], cal, tt);
+                    const cplx<T> tt = apply_A_elem<SP>(own[e][0], acc[e][0], kap, kapl);
+                    out[0] = a.op_only ? tt : minus_alpha<SP>(own[e][0], cal, call, tt);
                     if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), out[0]);
                     VecIO<S, 1>::st(po + (size_t)e * nb * 2, out);
                     if (YMODE == 1) {
                         cplx<T> yv[1];
                         yv[0] = cmul_f(cya, own[e][0]);
-                        cmac(yv[0], cyb, out[0]);
+                        if (SP) cmac(yv[0], cyal, own[e][0]);
+                        cmac2<SP>(yv[0], cyb, cybl, out[0]);
                         VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);
                     } else if (YMODE == 2) {
                         cplx<T> yv[1];
                         VecIO<S, 1>::ld(py + (size_t)e * nb * 2, yv);
-                        cmac(yv[0], cyb, out[0]);
+                        cmac2<SP>(yv[0], cyb, cybl, out[0]);
                         VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);
                     }
                 }
             } else {
                 const cplx<T> cb = Coef<T>::get(a.beta, a.betaf), cg = Coef<T>::get(a.gamma, a.gammaf);
+                const cplx<T> cbl = lo_of<T>(a.betal), cgl = lo_of<T>(a.gammal);
                 const S* pw = reinterpret_cast<const S*>(a.w) + off;
                 S* pwo = reinterpret_cast<S*>(a.wout) + off;
                 S* py = reinterpret_cast<S*>(a.y) + off;
@@ -179,10 +183,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
                     cplx<T> wv[1], yv[1];
                     VecIO<S, 1>::ld(pw + (size_t)e * nb * 2, wv);
                     VecIO<S, 1>::ld(py + (size_t)e * nb * 2, yv);
-                    const cplx<T> tt = minus_alpha(own[e][0], cal, apply_A_elem(own[e][0], acc[e][0], kap));
-                    const cplx<T> wn = minus_alpha(wv[0], cb, wv[0] - tt);
+                    const cplx<T> tt = minus_alpha<SP>(own[e][0], cal, call, apply_A_elem<SP>(own[e][0], acc[e][0], kap, kapl));
+                    const cplx<T> wn = minus_alpha<SP>(wv[0], cb, cbl, wv[0] - tt);
                     wv[0] = wn;
-                    cmac(yv[0], cg, wn);
+                    cmac2<SP>(yv[0], cg, cgl, wn);
                     if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), yv[0]);
                     VecIO<S, 1>::st(pwo + (size_t)e * nb * 2, wv);
                     VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);

@@ -84,6 +84,38 @@ def library_sampler(h, seed):
     return sample
 
 
+def full_estimate(h_inv, h_lev, eps, seed, pin, colours, ncolours, *, h_probe=None, chunk=16, rtol=1e-10, m=40,
+                  maxcycles=50, nmax=1 << 15):
+    """The whole multipolynomial estimate of Tr A^{-1} (Sec. 5, step 3 (a) - (e); Eq. (2)):
+
+        Tr A^{-1} = Tr(A^{-1} - p_1) + Tr(p_1 - p_2) + Tr(p_2 - p_3) + Tr(p_3).
+
+    The handles hold the polynomials p_1 = q_0, p_2 = q_1, p_3 = q_2 (and p_in,
+    a single polynomial, at index `pin` of h_inv).  The three Monte Carlos run one
+    after another with the sequential rule: Tr(A^{-1} - p_1) on the FP64 handle
+    h_inv (deflated PP-GMRES solves, mpmc_trace_inverse) to eps / sqrt(3) with
+    checks from two noises; the deflated difference levels on h_lev with the
+    checks 3, 6, ... and 6, 9, ...; then Tr(p_3) by probing with the given
+    colouring (exact when it is a distance-d colouring, d >= degree of p_3).
+    Returns {"levels": [...], "probing", "total", "err"}: total = the sum of the
+    three Monte Carlo estimates and the probing trace, err = their combined
+    standard error (currerr of step 3e).  nmax caps the noise vectors of each
+    Monte Carlo (a level that has not met its tolerance by then stops there)."""
+    def sample(level, first, count):
+        if level == "inverse":
+            mean, _, s = h_inv.mpmc_trace_inverse(0, seed, count, first, pin=pin, rtol=rtol, m=m,
+                                                  maxcycles=maxcycles)
+        else:
+            mean, _, s = h_lev.mpmc_trace_level(level, seed, count, first)
+        return s, mean - np.mean(s)
+    nlev = h_lev.nlevels
+    out = sequential_estimate(sample, ["inverse"] + list(range(nlev - 1)), eps, chunk=chunk, nmax=nmax)
+    probing = (h_probe or h_lev).mpmc_trace_probing_colours(nlev - 1, colours, ncolours)
+    out["probing"] = probing
+    out["total"] = out["total"] + probing
+    return out
+
+
 def allocation(variances, costs, eps):
     """Samples per level minimising the cost for total standard error eps (Eq. (3)):
     N_l = eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k); returns (N_l rounded up, cost)."""

@@ -73,6 +73,10 @@ _SIGS = {
     "mpmc_batch_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "mpmc_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "mpmc_trace_probing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "mpmc_colouring": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "mpmc_trace_probing_colours": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.c_void_p]),
     "mpmc_trace_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "mpmc_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -93,8 +97,14 @@ OPT_SWEEP_STENCIL = 2
 OPT_SWEEP_SEGMENT = 3
 OPT_FAST_STENCIL = 4
 OPT_FAST_SITES = 5
+OPT_WAIT_LIMIT = 6
+OPT_TEST_SKIP_COPY = 7
+OPT_SWEEP_ORDER = 8
 
 PROF_STENCIL, PROF_DEFLATION, PROF_OTHER = 0, 1, 2
+PROF_K_FSWEEP, PROF_K_FAST, PROF_K_SITE, PROF_K_SWEEP = 3, 4, 5, 6
+PROF_KERNEL_NAMES = {PROF_K_FSWEEP: "k_fsweep", PROF_K_FAST: "k_fast", PROF_K_SITE: "k_step/k_outer",
+                     PROF_K_SWEEP: "k_sweep"}
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -323,6 +333,17 @@ class Handle:
         self._check(self._L.mpmc_trace_probing(self._h, int(index), int(m), _ptr(t)), "mpmc_trace_probing")
         return complex(t[0])
 
+    def mpmc_trace_probing_colours(self, index, colours, ncolours):
+        """Probing estimate of Tr p(A) with a site colouring (exact when same-coloured
+        sites are more hops apart than the degree of p)."""
+        c = np.ascontiguousarray(colours, dtype=np.int32)
+        if c.size != self.V:
+            raise ValueError(f"colours must have {self.V} entries")
+        t = np.zeros(1, dtype=np.complex128)
+        self._check(self._L.mpmc_trace_probing_colours(self._h, int(index), _ptr(c), int(ncolours), _ptr(t)),
+                    "mpmc_trace_probing_colours")
+        return complex(t[0])
+
     def mpmc_trace_level(self, level, seed, nsamples, first=0):
         """(mean with exact correction, variance of Re, samples) of one level."""
         mean = np.zeros(1, dtype=np.complex128)
@@ -443,6 +464,20 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def mpmc_colouring(dims, distance):
+    """(colours, ncolours): a distance-`distance` colouring of the periodic lattice
+    dims = (Lx, Ly, Lz, Lt) from the library (host code, no GPU needed)."""
+    L = lib()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    V = int(np.prod(dims))
+    colours = np.zeros(V, dtype=np.int32)
+    nc = ctypes.c_int()
+    rc = L.mpmc_colouring(d, int(distance), _ptr(colours), ctypes.byref(nc))
+    if rc != MPMC_OK:
+        raise MpmcError(rc, "mpmc_colouring: " + L.mpmc_strerror(rc).decode())
+    return colours, nc.value
 
 
 def mpmc_trace_poly_noalloc(links, kappa, roots, seed, level, first, nsamples, out=None, bc_t=1, stream=None):

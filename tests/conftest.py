@@ -36,3 +36,26 @@ def dense(dims, kind="haar", seed=0, kappa=0.12, eps=0.3, bc_t=1):
 @pytest.fixture
 def rng():
     return np.random.Generator(np.random.PCG64(12345))
+
+
+def paired_bound(d, ref, noise_frac=0.3):
+    """The mixed-precision bound on identical noise, for the paired differences
+    d = s_mixed - s_64 of N samples and the FP64 samples ref (real parts):
+
+      bias:   |mean d| <= 0.1 SE_64 + 3 std(d) / sqrt(N)
+      noise:  std(d)   <= noise_frac std(s_64)        (skipped when noise_frac is None)
+
+    The bias test allows for the sampling noise of the N differences at three
+    standard deviations; a bias above a tenth of the FP64 standard error that
+    the pairing resolves fails it.  Returns (bias, allowed bias, noise ratio)."""
+    d = np.asarray(d).real
+    ref = np.asarray(ref).real
+    N = d.size
+    se = np.std(ref, ddof=1) / np.sqrt(N)
+    allowed = 0.1 * se + 3.0 * np.std(d, ddof=1) / np.sqrt(N)
+    bias = abs(np.mean(d))
+    ratio = np.std(d, ddof=1) / np.std(ref, ddof=1)
+    assert bias <= allowed, f"bias {bias:.3e} > {allowed:.3e} (SE64 {se:.3e}, std(d)/std64 {ratio:.3e})"
+    if noise_frac is not None:
+        assert ratio <= noise_frac, f"std(d)/std64 = {ratio:.3e} > {noise_frac}"
+    return bias, allowed, ratio

@@ -108,6 +108,56 @@ def test_batch_recaptures_after_plain_calls_reallocate_buffers():
             h.close()
 
 
+@pytest.mark.parametrize("prec", [G.FP64, G.FP32])
+def test_batch_instances_match_the_oracle(prec):
+    """One instance of each cheap lattice class of the 64-instance batch (4^4 and
+    6^4: near-identity links, its own kappa, composite 15 x 20, degrees 40 and 8,
+    32 noises), with roots from the oracle's setup, run as a batch: each level's
+    mean equals the oracle's mean over the same noise, to 1e-12 of the summed
+    terms in FP64, and within the paired bias bound in FP32 (the differences of
+    the per-sample values of the same handle traced alone, which the batch
+    reproduces bit for bit, against the oracle's samples)."""
+    from conftest import paired_bound
+    from oracle import krylov as K
+    from oracle import mpmc as M
+    from oracle.lattice import WilsonOperator
+    from paper_2306_09559_gb300 import synth, workloads
+    from test_gpu_parity import set_polys
+    insts = workloads.batch_instances()
+    pick = [next(w for w in insts if w.dims == d) for d in ((4, 4, 4, 4), (6, 6, 6, 6))]
+    N, seed = 32, 7
+    hs, oracle = [], []
+    try:
+        for w in pick:
+            U = workloads.gauge(w)
+            op = WilsonOperator(U, w.kappa)
+            b0 = synth.random_unit_vector(op.n, w.setup_seed)
+            p40, p8, p_in = K.gmres_polynomials(op, b0, [40, 8, 14])
+            p_out, _, _ = K.pp_gmres_roots(op, p_in, b0, m_out=20)
+            polys = [{"kind": "composite", "inner": p_in, "outer": p_out},
+                     {"kind": "single", "roots": p40}, {"kind": "single", "roots": p8}]
+            h = G.Handle(U, w.kappa, prec)
+            set_polys(h, polys)
+            h.mpmc_set_block(N)
+            hs.append(h)
+            oracle.append([M.level_sample_parts(op, polys, l, seed, N) for l in range(3)])
+        alone = [h.mpmc_trace_levels(seed, N, 0)[2] for h in hs]
+        with G.Batch(hs) as b:
+            mean, _ = b.mpmc_batch_trace_levels(seed, N, 0)
+        for i in range(len(hs)):
+            for l in range(3):
+                ref, hi, lo, _ = oracle[i][l]
+                mag = np.mean(np.abs(hi) + np.abs(lo))
+                if prec == G.FP64:
+                    assert abs(mean[i, l] - ref.mean()) <= 1e-12 * mag, (i, l)
+                else:
+                    assert abs(mean[i, l] - alone[i][l].mean()) <= 1e-13 * mag, (i, l)
+                    paired_bound(alone[i][l] - ref, ref)
+    finally:
+        for h in hs:
+            h.close()
+
+
 def test_batch_rejects_bad_arguments():
     import ctypes
     L = G.lib()

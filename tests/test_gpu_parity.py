@@ -6,9 +6,8 @@ Tolerances:
     applies, 1e-12 relative per level sample (relative to the magnitude of
     the summed terms |b^H p_l b| + |b^H p_{l+1} b| + |deflation term|);
   * FP32 path: 3e-6 relative for A; for level samples the paired bound on
-    identical noise, |mean(s32 - s64)| <= 0.1 SE64 + f and
-    std(s32 - s64) <= 0.3 std(s64) + f, with the FP32 resolution floor
-    f = 1e-7 <|b^H p_l b| + |b^H p_{l+1} b|>;
+    identical noise (conftest.paired_bound): bias |mean(s32 - s64)| <=
+    0.1 SE64 + 3 std(s32 - s64)/sqrt(N), noise std(s32 - s64) <= 0.3 std(s64);
   * BF16-stored path: 1.5e-2 relative for A (inputs rounded to bf16).
 """
 
@@ -17,7 +16,7 @@ import functools
 import numpy as np
 import pytest
 
-from conftest import links, operator
+from conftest import links, operator, paired_bound
 from oracle import krylov as K
 from oracle import mpmc as M
 from oracle import philox
@@ -190,13 +189,7 @@ def test_trace_levels_fp32_paired_bound():
         _, _, s = h.mpmc_trace_levels(seed=99, nsamples=N)
     for level in range(3):
         ref, hi, lo, dt = M.level_sample_parts(op, polys, level, 99, N, defl)
-        d = s[level] - ref
-        se = np.std(ref.real, ddof=1) / np.sqrt(N)
-        # FP32 resolves the cancelling terms b^H p_l b and b^H p_{l+1} b only to
-        # ~1e-7 of their size: that floor is added to the paired bounds
-        floor = 1e-7 * np.mean(np.abs(hi) + np.abs(lo))
-        assert abs(np.mean(d.real)) <= 0.1 * se + floor, level
-        assert np.std(d.real) <= 0.3 * np.std(ref.real) + floor, level
+        paired_bound(s[level] - ref, ref)
 
 
 @pytest.mark.parametrize("prec", [G.FP64, G.FP32])
@@ -300,10 +293,7 @@ def test_trace_projected_composite_fp32_paired():
         set_polys(h, pp)
         _, _, s = h.mpmc_trace_levels(seed=9, nsamples=N)
     ref, hi, lo, dt = M.level_sample_parts(op, pp, 0, 9, N, defl)
-    d = s[0] - ref
-    floor = 1e-7 * np.mean(np.abs(hi) + np.abs(lo))
-    assert abs(np.mean(d.real)) <= 0.1 * np.std(ref.real, ddof=1) / np.sqrt(N) + floor
-    assert np.std(d.real) <= 0.3 * np.std(ref.real) + floor
+    paired_bound(s[0] - ref, ref)
 
 
 def test_projected_composite_only_at_the_top():
