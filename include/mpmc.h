@@ -130,16 +130,26 @@ MPMC_API int mpmc_set_block(mpmc_handle h, int nrhs_block);
  * p_in(A) p_out(A p_in(A)) of degree nroots*nouter - 1 (Sec. 3.2).  The
  * deflated kind adds the projection of Sec. 4.3 with the eigenpairs of
  * mpmc_set_deflation (which must be called first).
- * leja != 0 reorders each root list into modified Leja order (first the
- * root of largest modulus, then each next root maximising the product of
- * distances to those taken; ties to the lowest index); leja = 0 keeps the
- * caller's order.
+ * leja: flags.  Bit 0 (MPMC_POLY_LEJA) reorders each root list into
+ * modified Leja order (first the root of largest modulus, then each next root
+ * maximising the product of distances to those taken; ties to the lowest
+ * index); without it the caller's order is kept.  Bit 1
+ * (MPMC_POLY_FP32_COEFS) replaces every root theta by 1/c with c = 1/theta
+ * rounded to the nearest FP32 complex number, on any handle.  The product
+ * form applies the coefficients 1/theta; FP32 and BF16S handles apply them in
+ * FP32, so without this flag they use the polynomial with those rounded roots
+ * while an FP64 handle uses the exact one.  With it, handles of every
+ * precision apply the same polynomial, and the traces of a reduced-precision
+ * estimate differ from FP64 ones only by arithmetic rounding (a root moves
+ * by at most ~6e-8 of its modulus).
  * Polynomials 0..L-1 define the levels of mpmc_trace_levels: level l < L-1
  * is Tr(p_l - p_{l+1}), level L-1 is Tr(p_{L-1}) (Eq. (2)).
  * Errors: EINVAL (index, kind, counts, NULL roots), ENONFINITE (a root is
  * zero or not finite), ESTATE (deflated kind without deflation).
  */
 #define MPMC_MAX_POLYS 8
+#define MPMC_POLY_LEJA 1
+#define MPMC_POLY_FP32_COEFS 2
 MPMC_API int mpmc_set_poly(mpmc_handle h, int index, int kind,
                   const double* roots, int nroots,
                   const double* outer, int nouter, int leja);
@@ -444,6 +454,17 @@ MPMC_API int mpmc_trace_probing(mpmc_handle h, int index, int m, double* trace);
  * range, ncolours < 1), ESTATE, ENOTSUP as mpmc_trace_probing.
  */
 MPMC_API int mpmc_colouring(const int dims[4], int distance, int* colours, int* ncolours);
+
+/*
+ * mpmc_fma_peak: measured FMA throughput of the CUDA cores of the current
+ * device in TFLOP/s (2 flops per FMA), for precision MPMC_FP64 or MPMC_FP32:
+ * independent FMA chains on every SM, timed with CUDA events after a warm-up
+ * launch.  The ALU roofline of the FP64 stencil path, which is bound by FP64
+ * arithmetic rather than HBM on GB300.  The paper has no counterpart (it
+ * reports desktop-CPU wall times only).  Allocates one small device buffer.
+ * Errors: EINVAL (NULL), ENOTSUP (precision), ENOMEM, ECUDA.
+ */
+MPMC_API int mpmc_fma_peak(int precision, double* tflops);
 MPMC_API int mpmc_trace_probing_colours(mpmc_handle h, int index, const int* colours, int ncolours,
                                         double* trace);
 

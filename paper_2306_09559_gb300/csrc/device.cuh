@@ -58,6 +58,40 @@ __device__ __forceinline__ void st(__nv_bfloat16* p, cplx<float> a) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a.re, a.im);
 }
 
+// ------------------------------------------------------------------ stochastic rounding to BF16
+// Round-to-nearest of the chain vectors to BF16 leaves an error that is a fixed function of the
+// stored value; when the values follow the noise vector (w = c b + neighbour terms) the error
+// correlates with b and b^H p(A) b acquires a bias of ~1e-3 of its size.  The BF16 chain stores
+// therefore round stochastically (the hardware conversion with random bits): up or down with
+// probabilities that make every rounding error zero-mean given the value, so the chain's
+// expectation is that of the unrounded arithmetic.  The random bits are a hash of the element
+// index and a per-step salt: results stay deterministic.
+__device__ __forceinline__ uint32_t sr_hash(uint32_t x) {   // integer mixing (xor-shift-multiply)
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// (re, im) -> two BF16 rounded stochastically with the random bits rb; re in the low half
+__device__ __forceinline__ uint32_t bf16x2_sr(float re, float im, uint32_t rb) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(im), "f"(re), "r"(rb));
+    return d;
+}
+// Stores of a storage format with stochastic rounding where it narrows (BF16); exact otherwise
+__device__ __forceinline__ void st_sr(double* p, cplx<double> a, uint32_t) { st(p, a); }
+__device__ __forceinline__ void st_sr(float* p, cplx<float> a, uint32_t) { st(p, a); }
+__device__ __forceinline__ void st_sr(__nv_bfloat16* p, cplx<float> a, uint32_t rb) {
+    *reinterpret_cast<uint32_t*>(p) = bf16x2_sr(a.re, a.im, rb);
+}
+// random bits of component e of the element group whose hash is h (one hash per site and column)
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int e) { return h + (uint32_t)e * 0x9E3779B9u; }
+__device__ __forceinline__ uint32_t sr_seed(uint32_t salt, uint32_t site, uint32_t col) {
+    return sr_hash(salt ^ sr_hash(site * 0x27d4eb2fu + col));
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers
 // 0xD2511F53 and 0xCD9E8D57, key increments 0x9E3779B9 and 0xBB67AE85,

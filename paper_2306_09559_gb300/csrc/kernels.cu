@@ -90,30 +90,24 @@ __global__ void k_export(size_t nrow, const S* __restrict__ src, int nb, double*
 }
 
 template <class S>
-__global__ void k_scale(size_t n, const S* __restrict__ in, double sre, double sim, S* out) {
+__global__ void k_scale(size_t n, const S* __restrict__ in, double sre, double sim, S* out, uint32_t salt) {
     using T = typename Math<S>::T;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     const cplx<T> sc = {T(sre), T(sim)};
-    const cplx<T> x = ld(in + idx * 2);
-    cplx<T> r = mul(sc, x);
-    if (sizeof(T) == 4) {   // the scale as an FP32 hi + lo pair (hi is sc)
-        const cplx<T> lo = {T(sre - (double)sc.re), T(sim - (double)sc.im)};
-        r = r + mul(lo, x);
-    }
-    st(out + idx * 2, r);
+    st_sr(out + idx * 2, mul(sc, ld(in + idx * 2)), sr_hash(salt ^ sr_hash((uint32_t)idx)));
 }
 
 template <class T>
-__global__ void k_links(int V, const double* __restrict__ src, T* dst) {
+__global__ void k_links(int V, const double* __restrict__ src, double scale, T* dst) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu, i)
     if (idx >= (size_t)V * 36) return;
     const int i = (int)(idx % 9);
     const int mu = (int)((idx / 9) % 4);
     const size_t site = idx / 36;
     const double* p = src + (((size_t)mu * V + site) * 9 + i) * 2;
-    dst[idx * 2] = (T)p[0];
-    dst[idx * 2 + 1] = (T)p[1];
+    dst[idx * 2] = (T)(scale * p[0]);
+    dst[idx * 2 + 1] = (T)(scale * p[1]);
 }
 
 template <class T>
@@ -440,28 +434,20 @@ LaunchCfg chain_config(const Geom& g, int nb, int bx_max, int sl, int R) {
 
 void fill_floats(StepArgs& a) {
     for (int i = 0; i < 2; ++i) {
-        a.alphaf[i] = f32_hi(a.alpha[i]);
-        a.yaf[i] = f32_hi(a.ya[i]);
-        a.ybf[i] = f32_hi(a.yb[i]);
-        a.alphal[i] = f32_lo(a.alpha[i]);
-        a.yal[i] = f32_lo(a.ya[i]);
-        a.ybl[i] = f32_lo(a.yb[i]);
+        a.alphaf[i] = (float)a.alpha[i];
+        a.yaf[i] = (float)a.ya[i];
+        a.ybf[i] = (float)a.yb[i];
     }
-    a.kappaf = f32_hi(a.kappa);
-    a.kappal = f32_lo(a.kappa);
+    a.kappaf = (float)a.kappa;
 }
 
 void fill_floats(OuterArgs& a) {
     for (int i = 0; i < 2; ++i) {
-        a.alphaf[i] = f32_hi(a.alpha[i]);
-        a.betaf[i] = f32_hi(a.beta[i]);
-        a.gammaf[i] = f32_hi(a.gamma[i]);
-        a.alphal[i] = f32_lo(a.alpha[i]);
-        a.betal[i] = f32_lo(a.beta[i]);
-        a.gammal[i] = f32_lo(a.gamma[i]);
+        a.alphaf[i] = (float)a.alpha[i];
+        a.betaf[i] = (float)a.beta[i];
+        a.gammaf[i] = (float)a.gamma[i];
     }
-    a.kappaf = f32_hi(a.kappa);
-    a.kappal = f32_lo(a.kappa);
+    a.kappaf = (float)a.kappa;
 }
 
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns, const StepArgs& a0,
@@ -512,16 +498,18 @@ void launch_export(int storage, int V, const void* src, int nb, double* dst, int
     else k_export<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(nrow, (const __nv_bfloat16*)src, nb, dst, ld_, c0, cnt);
 }
 
-void launch_scale(int storage, size_t n, const void* in, const double sc[2], void* out, cudaStream_t s) {
-    if (storage == ST_F64) k_scale<double><<<blocks_for(n, 256), 256, 0, s>>>(n, (const double*)in, sc[0], sc[1], (double*)out);
-    else if (storage == ST_F32) k_scale<float><<<blocks_for(n, 256), 256, 0, s>>>(n, (const float*)in, sc[0], sc[1], (float*)out);
-    else k_scale<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(n, (const __nv_bfloat16*)in, sc[0], sc[1], (__nv_bfloat16*)out);
+void launch_scale(int storage, size_t ncplx, const void* in, const double sc[2], void* out, cudaStream_t s,
+                  uint32_t salt) {
+    const size_t n = ncplx;
+    if (storage == ST_F64) k_scale<double><<<blocks_for(n, 256), 256, 0, s>>>(n, (const double*)in, sc[0], sc[1], (double*)out, salt);
+    else if (storage == ST_F32) k_scale<float><<<blocks_for(n, 256), 256, 0, s>>>(n, (const float*)in, sc[0], sc[1], (float*)out, salt);
+    else k_scale<__nv_bfloat16><<<blocks_for(n, 256), 256, 0, s>>>(n, (const __nv_bfloat16*)in, sc[0], sc[1], (__nv_bfloat16*)out, salt);
 }
 
-void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s) {
+void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s, double scale) {
     const size_t n = (size_t)V * 36;
-    if (storage == ST_F64) k_links<double><<<blocks_for(n, 256), 256, 0, s>>>(V, src, (double*)dst);
-    else k_links<float><<<blocks_for(n, 256), 256, 0, s>>>(V, src, (float*)dst);
+    if (storage == ST_F64) k_links<double><<<blocks_for(n, 256), 256, 0, s>>>(V, src, scale, (double*)dst);
+    else k_links<float><<<blocks_for(n, 256), 256, 0, s>>>(V, src, scale, (float*)dst);
 }
 
 void launch_convert_vectors(int storage, size_t ncplx, const double* src, void* dst, cudaStream_t s) {

@@ -36,10 +36,8 @@ struct StepArgs {
     double dot_w[2];
     double2* acc;
     double kappa;
-    // the same in FP32 as hi + lo pairs (filled by launch_step): hi = fl32(c), lo = fl32(c - hi),
-    // so that FP32 kernels apply every coefficient to ~1e-15 relative, not rounded to FP32
-    float alphaf[2], yaf[2], ybf[2], kappaf;
-    float alphal[2], yal[2], ybl[2], kappal;
+    float alphaf[2], yaf[2], ybf[2], kappaf;   // the same in FP32 (filled by launch_step)
+    uint32_t salt;                              // random-bit salt of stochastically rounded BF16 stores
 };
 
 // Last inner step of a composite outer step (Sec. 3.2):
@@ -56,8 +54,8 @@ struct OuterArgs {
     double dot_w[2];
     double2* acc;
     double kappa;
-    float alphaf[2], betaf[2], gammaf[2], kappaf;   // hi parts (as StepArgs)
-    float alphal[2], betal[2], gammal[2], kappal;   // lo parts
+    float alphaf[2], betaf[2], gammaf[2], kappaf;
+    uint32_t salt;                              // as StepArgs
 };
 
 struct LaunchCfg {
@@ -76,11 +74,9 @@ void outer_f64(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&
 void outer_f32(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 void outer_bf16(const Geom&, const void*, int, const NoiseSpec&, const OuterArgs&, const LaunchCfg&, cudaStream_t);
 
-// FP32 hi + lo copies of the coefficients (what the FP32 / BF16 kernels use)
+// FP32 copies of the coefficients (what the FP32 / BF16 kernels use)
 void fill_floats(StepArgs& a);
 void fill_floats(OuterArgs& a);
-inline float f32_hi(double c) { return (float)c; }
-inline float f32_lo(double c) { return (float)(c - (double)(float)c); }
 
 void launch_step(int storage, const Geom& g, const void* links, int nb, const NoiseSpec& ns,
                  const StepArgs& a, const LaunchCfg& cfg, cudaStream_t s);
@@ -107,8 +103,8 @@ struct FastArgs {
     const float4* Ue;        // expanded links [V][4][9] (re, re, im, im)
     double2* acc;
     double dot_w[2];
-    float alpha[2], beta[2], gamma[2], kappa;            // hi parts: fl32(c)
-    float alpha_lo[2], beta_lo[2], gamma_lo[2], kappa_lo; // lo parts: fl32(c - hi)
+    float alpha[2], beta[2], gamma[2], kappa;
+    uint32_t salt;                   // random-bit salt of stochastically rounded BF16 stores
     int lx, ly, lz, lt, V, bc_t, sl;
     unsigned long long mx, my, mz;   // floor(2^64 / extent) + 1
     const int* blk_order;            // t-sweep: site block of each launch-order index (null: plain order)
@@ -136,8 +132,8 @@ int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepC
                   cudaStream_t s, bool lsm);
 // Z4 words of a noise block: words[site][col] = Philox word 0 of (j0 + col, site, level)
 void launch_noise_words(const Geom& g, int nb, const NoiseSpec& ns, uint32_t* words, cudaStream_t s);
-// expanded links (re, re, im, im) in float from complex-double [mu][site][3][3]
-void launch_links_expanded(int V, const double* src, float4* dst, cudaStream_t s);
+// expanded links (re, re, im, im) in float from scale * complex-double [mu][site][3][3]
+void launch_links_expanded(int V, const double* src, float4* dst, cudaStream_t s, double scale = 1.0);
 
 // t-sweep form of the step / outer kernels (stencil_sweep.cu): FP32 and
 // BF16 storage, even lx, ly, lz; the input block is read by TMA through a
@@ -164,9 +160,12 @@ void launch_import(int storage, int V, const double* src, int ld, int c0, int cn
 void launch_export(int storage, int V, const void* src, int nb, double* dst, int ld, int c0, int cnt,
                    cudaStream_t s);
 // out = s * in (storage buffers of V*12*nb complex)
-void launch_scale(int storage, size_t ncplx, const void* in, const double sc[2], void* out, cudaStream_t s);
-// links: complex double [mu][site][3][3] -> math precision [site][mu][3][3]
-void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s);
+// (BF16 output rounded stochastically with random bits salted by `salt`)
+void launch_scale(int storage, size_t ncplx, const void* in, const double sc[2], void* out, cudaStream_t s,
+                  uint32_t salt = 0);
+// links: scale * complex double [mu][site][3][3] -> math precision [site][mu][3][3] (the product
+// formed in FP64, then rounded once per element)
+void launch_links(int storage, int V, const double* src, void* dst, cudaStream_t s, double scale = 1.0);
 
 // samples[j0 + col] = sum_cta acc_hi + const_hi - (sum_cta acc_lo + const_lo) - dterm[col]
 // also hi/lo parts (may be null).  acc_lo/dterm may be null.
@@ -183,8 +182,10 @@ void launch_proj_coef(int k, int nb, const int* pair, const double2* inv_d, cons
                       const double2* G2, double2* D64, float2* D32, double2* xz, cudaStream_t s);
 void launch_rank_update(int math, int storage, int V, int nb, const void* Y, int k, const double2* D64,
                         const float2* D32, double sign, const void* base, const NoiseSpec& ns, void* out,
-                        cudaStream_t s);
-void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s);
+                        cudaStream_t s, uint32_t salt = 0);
+// vector-major [k][V*12] -> block layout [site][e][k] in the math precision; src_storage: the
+// precision of src (default: math; FP32 src with FP64 math is widened exactly)
+void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s, int src_storage = -1);
 // out[c] = (|x_c|^2, |y_c|^2, Re x_c^H y_c, Im x_c^H y_c) for FP64 blocks of nb columns
 void launch_col_stats(int V, int nb, const double* X, const double* Y, double* part, int nsplit, double* out,
                       cudaStream_t s);

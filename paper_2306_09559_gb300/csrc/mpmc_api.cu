@@ -108,7 +108,8 @@ struct mpmc_ctx {
     // t-sweep stencil: option, t-segment length (0 automatic), tensor maps of input buffers
     // Stencil step classes: bit 0 dotted steps (single / projected chains, incl. the noise-started
     // first step), bit 1 undotted steps (inner steps of composite chains), bit 2 outer steps.
-    int use_sweep = 7;            // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep
+    int use_sweep = 23;           // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep;
+                                  // bit 4: that form with each plane's links staged in shared memory
     int sweep_ts = 0;
     int use_fast = 7;             // issue-lean kernels per class (FP32 / BF16S, block widths 16 .. 1024)
     int fast_sl = 1;              // sites per thread of the issue-lean kernels
@@ -130,6 +131,10 @@ struct mpmc_ctx {
     double* kr_nrm = nullptr;
     int kr_m = 0;
     long long launches = 0;
+    // stochastic rounding of BF16 chain stores: salt of the current chain (from its noise block and
+    // polynomial) and the position of the next step in it, so that a call's random bits depend on
+    // what it computes, not on the handle's history
+    uint32_t sr_base = 0, sr_step = 0;
     double2* probe = nullptr;     // probing: [nchunk][nb] partial sums + 1 total
     size_t probe_cap = 0;
     int* probe_tab = nullptr;     // probing: site colours of the caller's colouring
@@ -273,6 +278,13 @@ int ensure_ws(mpmc_ctx* h, Workspace& w, int storage, int nb) {
 
 const void* links_for(const mpmc_ctx* h, int storage) { return storage == ST_F64 ? h->links64 : h->links32; }
 
+// kappa as the stencil kernels of a storage format take it.  The reduced-precision links
+// are stored premultiplied by kappa (kappa U, formed in FP64 and rounded once per element),
+// so those kernels apply A = I - (kappa H) with kappa = 1: a rounded kappa would shift the
+// matrix by the same relative amount at every site, a systematic change of every trace,
+// while per-element rounding of kappa U varies in sign from element to element.
+double kap(const mpmc_ctx* h, int storage) { return storage == ST_F64 ? h->kappa : 1.0; }
+
 
 // ------------------------------------------------------------------ profiling
 int prof_begin(mpmc_ctx* h, int cls, double bytes) {
@@ -354,6 +366,22 @@ const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in, int kind
     return h->maps.back().m;
 }
 
+uint32_t mix32(uint32_t x) {   // integer mixing for the stochastic-rounding salts
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// Start of a chain: its salt from the noise block (or none, in apply mode) and the polynomial.
+void begin_chain(mpmc_ctx* h, const NoiseSpec& ns, uint32_t poly_tag) {
+    h->sr_base = mix32((uint32_t)ns.seed ^ mix32((uint32_t)(ns.seed >> 32) ^ mix32(ns.level ^ mix32(ns.j0 ^
+                                                                                mix32(poly_tag)))));
+    h->sr_step = 0;
+}
+uint32_t next_salt(mpmc_ctx* h) { return mix32(h->sr_base + 0x9E3779B9u * (h->sr_step++)); }
+
 // Z4 word table of the noise block `ns` for the issue-lean kernels (made when the block changes).
 int ensure_words(mpmc_ctx* h, Workspace& ws, const NoiseSpec& ns) {
     if (ws.words_ok && ws.words_ns.seed == ns.seed && ws.words_ns.level == ns.level && ws.words_ns.j0 == ns.j0)
@@ -374,8 +402,7 @@ FastArgs fast_args(const mpmc_ctx* h, const Workspace& ws, double kappa) {
     f.wait_limit = h->wait_limit;
     f.blk_order = h->sweep_order ? h->blk_order : nullptr;
     f.skip_copy = h->skip_copy;
-    f.kappa = f32_hi(kappa);
-    f.kappa_lo = f32_lo(kappa);
+    f.kappa = (float)kappa;
     return f;
 }
 
@@ -389,15 +416,14 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         const int kind = a.in ? (a.dot ? 1 : 0) : 2;
         if (kind) if (int rc = ensure_words(h, ws, ns)) return rc;
         FastArgs f = fast_args(h, ws, a.kappa);
+        f.salt = a.salt;
         f.in = a.in;
         f.out = a.out;
         f.acc = a.acc;
         f.dot_w[0] = a.dot_w[0];
         f.dot_w[1] = a.dot_w[1];
-        for (int i = 0; i < 2; ++i) {
-            f.alpha[i] = f32_hi(a.alpha[i]);
-            f.alpha_lo[i] = f32_lo(a.alpha[i]);
-        }
+        f.alpha[0] = (float)a.alpha[0];
+        f.alpha[1] = (float)a.alpha[1];
         const bool lsm = (h->use_sweep & 16) != 0;
         const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, lsm ? 2 : 1)
                                                                             : nullptr;
@@ -422,7 +448,9 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
     return MPMC_OK;
 }
 
-int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& ns) {
+int do_step(mpmc_ctx* h, Workspace& ws, const StepArgs& a0, const NoiseSpec& ns) {
+    StepArgs a = a0;
+    a.salt = next_salt(h);
     const int reads = (a.in ? 1 : 0) + (a.ymode == 2 ? 1 : 0);
     const int writes = 1 + (a.ymode ? 1 : 0);
     const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * (reads + writes) + link_bytes(h, ws.storage);
@@ -438,6 +466,7 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
     if (ws.fast && (h->use_fast & 4)) {
         if (o.dot) if (int rc = ensure_words(h, ws, ns)) return rc;
         FastArgs f = fast_args(h, ws, o.kappa);
+        f.salt = o.salt;
         f.in = o.in;
         f.w = o.w;
         f.out = o.wout;
@@ -446,12 +475,9 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
         f.dot_w[0] = o.dot_w[0];
         f.dot_w[1] = o.dot_w[1];
         for (int i = 0; i < 2; ++i) {
-            f.alpha[i] = f32_hi(o.alpha[i]);
-            f.beta[i] = f32_hi(o.beta[i]);
-            f.gamma[i] = f32_hi(o.gamma[i]);
-            f.alpha_lo[i] = f32_lo(o.alpha[i]);
-            f.beta_lo[i] = f32_lo(o.beta[i]);
-            f.gamma_lo[i] = f32_lo(o.gamma[i]);
+            f.alpha[i] = (float)o.alpha[i];
+            f.beta[i] = (float)o.beta[i];
+            f.gamma[i] = (float)o.gamma[i];
         }
         const bool lsm = (h->use_sweep & 16) != 0;
         const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, lsm ? 2 : 1) : nullptr;
@@ -476,7 +502,9 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
     return MPMC_OK;
 }
 
-int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec& ns) {
+int do_outer(mpmc_ctx* h, Workspace& ws, const OuterArgs& o0, const NoiseSpec& ns) {
+    OuterArgs o = o0;
+    o.salt = next_salt(h);
     const double bytes = (double)h->g.V * ws.nb * 12 * storage_bytes(ws.storage) * 5 + link_bytes(h, ws.storage);
     if (int rc = prof_begin(h, PROF_STENCIL, bytes)) return rc;
     if (int rc = outer_launch(h, ws, o, ns)) return rc;
@@ -547,15 +575,19 @@ int num_levels(const mpmc_ctx* h) {
 
 inline void setc(double (&d)[2], cd z) { d[0] = z.real(); d[1] = z.imag(); }
 
-// A coefficient as the kernels of a storage format apply it.  Reduced-precision
-// kernels take every coefficient (kappa, 1/theta, 1/eta, scales) as an FP32
-// hi + lo pair and apply both parts, so they use the FP64 value to ~1e-15 and
-// the chain applies the same matrix and polynomial as the FP64 path: rounding
-// a coefficient to FP32 would shift the matrix or a root by ~6e-8 for every
-// vector alike, a systematic change of the traces that no number of noise
-// vectors averages out.  The host therefore weights their results with the
-// FP64 values themselves.
-inline cd rnd(int, cd z) { return z; }
+// A coefficient as the kernels of a storage format apply it: reduced-precision
+// kernels use the FP32 value, so the host uses the same value wherever it
+// weights their results (dot weights, closed-form terms).  The chain then
+// applies exactly (up to arithmetic rounding) the polynomial with roots
+// 1/rnd(1/theta); a correction term below half an FP32 ulp of the result would be
+// lost in its rounding, so the coefficients are not split further.  Roots given
+// with MPMC_POLY_FP32_COEFS have rnd(1/theta) = 1/theta on every handle, and
+// kappa reaches these kernels through links premultiplied by kappa (kappa = 1 in
+// the kernels), so that no coefficient is rounded for one precision only.
+inline cd rnd(int storage, cd z) {
+    if (storage == ST_F64) return z;
+    return cd((double)(float)z.real(), (double)(float)z.imag());
+}
 
 // ------------------------------------------------------------------ chains
 // Trace mode: acc += sum of weighted b^H w over all steps of p(A) applied to
@@ -563,6 +595,7 @@ inline cd rnd(int, cd z) { return z; }
 // b^H w_0 term known in closed form (b^H b = 12 V for noise starts).
 int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& ns, const void* start,
                 double2* acc, cd* cst) {
+    begin_chain(h, ns, (uint32_t)(&p - h->polys));
     const int st = ws.storage, nb = ws.nb;
     const void* U = links_for(h, st);
     const double n = (double)nsites12(h);
@@ -582,7 +615,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             a.dot = true;
             const cd al = 1.0 / th[j - 1];
             setc(a.alpha, rnd(st, al));
-            a.kappa = h->kappa;
+            a.kappa = kap(h, st);
             setc(a.dot_w, rnd(st, 1.0 / th[j]));
             a.acc = acc;
             if (int rc = do_step(h, ws, a, ns)) return rc;
@@ -614,7 +647,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
     {
         double s1[2];
         setc(s1, rnd(st, 1.0 / eta[0]));
-        launch_scale(st, ncplx, Wcur, s1, ws.y, h->stream);
+        launch_scale(st, ncplx, Wcur, s1, ws.y, h->stream, next_salt(h));
         LAUNCHED(1);
     }
     if (m_out == 1) {
@@ -632,7 +665,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
             a.dot = false;
             const cd al = 1.0 / th[j - 1];
             setc(a.alpha, rnd(st, al));
-            a.kappa = h->kappa;
+            a.kappa = kap(h, st);
             if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
@@ -643,7 +676,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         o.y = ws.y;
         const cd al = 1.0 / th[m_in - 1];
         setc(o.alpha, rnd(st, al));
-        o.kappa = h->kappa;
+        o.kappa = kap(h, st);
         setc(o.beta, rnd(st, 1.0 / eta[k - 1]));
         setc(o.gamma, rnd(st, 1.0 / eta[k]));
         o.dot = (k == m_out - 1);
@@ -664,7 +697,7 @@ int chain_trace(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const NoiseSpec& n
         a.dot = true;
         const cd al = 1.0 / th[j - 1];
         setc(a.alpha, rnd(st, al));
-        a.kappa = h->kappa;
+        a.kappa = kap(h, st);
         setc(a.dot_w, rnd(st, 1.0 / th[j]));
         a.acc = acc;
         if (int rc = do_step(h, ws, a, ns)) return rc;
@@ -683,7 +716,7 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
     if (m == 1) {
         double s1[2];
         setc(s1, rnd(st, 1.0 / th[0]));
-        launch_scale(st, ncplx, in0, s1, X, h->stream);
+        launch_scale(st, ncplx, in0, s1, X, h->stream, next_salt(h));
         LAUNCHED(1);
         return MPMC_OK;
     }
@@ -697,7 +730,7 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
         a.dot = false;
         const cd al = 1.0 / th[j - 1];
         setc(a.alpha, rnd(st, al));
-        a.kappa = h->kappa;
+        a.kappa = kap(h, st);
         setc(a.ya, rnd(st, 1.0 / th[0]));
         setc(a.yb, rnd(st, 1.0 / th[j]));
         if (int rc = do_step(h, ws, a, ns)) return rc;
@@ -707,6 +740,7 @@ int chain_apply_single(mpmc_ctx* h, Workspace& ws, const std::vector<cd>& th, co
 }
 
 int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, void* X) {
+    begin_chain(h, NoiseSpec{0, 0xA991u, 0}, (uint32_t)(&p - h->polys));
     if (p.kind == MPMC_SINGLE) return chain_apply_single(h, ws, p.roots, in0, X);
     const int st = ws.storage, nb = ws.nb;
     const void* U = links_for(h, st);
@@ -717,7 +751,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
     const size_t ncplx = (size_t)h->g.V * 12 * nb;
     double s1[2];
     setc(s1, rnd(st, 1.0 / eta[0]));
-    launch_scale(st, ncplx, in0, s1, ws.y, h->stream);
+    launch_scale(st, ncplx, in0, s1, ws.y, h->stream, next_salt(h));
     LAUNCHED(1);
     const void* Wcur = in0;
     void* Wnxt = ws.w[2];
@@ -729,7 +763,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
             a.out = ws.w[(j - 1) % 2];
             const cd al = 1.0 / th[j - 1];
             setc(a.alpha, rnd(st, al));
-            a.kappa = h->kappa;
+            a.kappa = kap(h, st);
             if (int rc = do_step(h, ws, a, ns)) return rc;
             in = a.out;
         }
@@ -740,7 +774,7 @@ int chain_apply(mpmc_ctx* h, Workspace& ws, const PolyDef& p, const void* in0, v
         o.y = ws.y;
         const cd al = 1.0 / th[m_in - 1];
         setc(o.alpha, rnd(st, al));
-        o.kappa = h->kappa;
+        o.kappa = kap(h, st);
         setc(o.beta, rnd(st, 1.0 / eta[k - 1]));
         setc(o.gamma, rnd(st, 1.0 / eta[k]));
         o.dot = false;
@@ -757,7 +791,7 @@ int apply_A(mpmc_ctx* h, Workspace& ws, const void* in, void* out) {
     a.in = in;
     a.out = out;
     a.op_only = true;
-    a.kappa = h->kappa;
+    a.kappa = kap(h, ws.storage);
     const NoiseSpec ns{0, 0, 0};
     return do_step(h, ws, a, ns);
 }
@@ -896,7 +930,12 @@ bool invert(std::vector<cd>& a, int k) {
     return true;
 }
 
-int proj_math(const mpmc_ctx* h) { return h->storage == ST_F64 ? ST_F64 : ST_F32; }
+// Arithmetic of the projection of the projected composite (Sec. 4.3) on every handle: FP64.  Z, A Z
+// and H^{-1} are formed once per deflation set and used for every noise vector, so an FP32 rounding
+// of them would be one fixed change of the operator M_1 shared by all samples (a shift of the
+// level's trace); in FP64 only the per-vector rounding of r = b - (A Z) D to the storage format
+// remains.  The cost is k complex multiply-adds per site and vector, once per chain.
+int proj_math(const mpmc_ctx*) { return ST_F64; }
 
 int ensure_gram_part(mpmc_ctx* h, size_t entries) {
     if (h->gram_part_cap >= entries) return MPMC_OK;
@@ -920,13 +959,13 @@ int ensure_projection(mpmc_ctx* h) {
     dev_free(h->d_Hinv);
     if (int rc = dev_alloc(h, &h->Zb, bytes)) return rc;
     if (int rc = dev_alloc(h, &h->Wb, bytes)) return rc;
-    launch_vec_to_block(math, h->g.V, k, h->Z, h->Zb, h->stream);
+    launch_vec_to_block(math, h->g.V, k, h->Z, h->Zb, h->stream, h->storage == ST_F64 ? ST_F64 : ST_F32);
     LAUNCHED(1);
     StepArgs a{};
     a.in = h->Zb;
     a.out = h->Wb;
     a.op_only = true;
-    a.kappa = h->kappa;
+    a.kappa = kap(h, math);
     const NoiseSpec ns0{0, 0, 0};
     launch_step(math, h->g, links_for(h, math), k, ns0, a, chain_config(h->g, k, 64, 1, 1), h->stream);
     LAUNCHED(1);
@@ -1056,9 +1095,9 @@ int mpmc_create(mpmc_handle* out, const int dims[4], const double* links, double
     launch_links(ST_F64, h->g.V, staging, h->links64, h->stream);
     if (h->storage != ST_F64) {
         if ((rc = dev_alloc(h, &h->links32, nl * 8))) { dev_free(staging); return bail(rc); }
-        launch_links(ST_F32, h->g.V, staging, h->links32, h->stream);
+        launch_links(ST_F32, h->g.V, staging, h->links32, h->stream, h->kappa);
         if ((rc = dev_alloc(h, &h->links_ex, nl * 16))) { dev_free(staging); return bail(rc); }
-        launch_links_expanded(h->g.V, staging, h->links_ex, h->stream);
+        launch_links_expanded(h->g.V, staging, h->links_ex, h->stream, h->kappa);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         dev_free(staging);
@@ -1135,7 +1174,20 @@ int mpmc_set_poly(mpmc_handle h, int index, int kind, const double* roots, int n
         if (!finite(z) || z == 0.0) return fail(h, MPMC_ENONFINITE, "root is zero or not finite");
     for (const cd& z : p.outer)
         if (!finite(z) || z == 0.0) return fail(h, MPMC_ENONFINITE, "outer root is zero or not finite");
-    if (leja) {
+    if (leja & MPMC_POLY_FP32_COEFS) {
+        // theta -> 1 / fl32(1 / theta): the coefficient every precision applies is an FP32 number
+        auto snap = [](cd z) {
+            const cd c = 1.0 / z;
+            return 1.0 / cd((double)(float)c.real(), (double)(float)c.imag());
+        };
+        for (cd& z : p.roots) z = snap(z);
+        for (cd& z : p.outer) z = snap(z);
+        for (const cd& z : p.roots)
+            if (!finite(z)) return fail(h, MPMC_ENONFINITE, "root outside the FP32 range");
+        for (const cd& z : p.outer)
+            if (!finite(z)) return fail(h, MPMC_ENONFINITE, "outer root outside the FP32 range");
+    }
+    if (leja & MPMC_POLY_LEJA) {
         auto o = leja_order(p.roots);
         std::vector<cd> r(p.roots.size());
         for (size_t i = 0; i < o.size(); ++i) r[i] = p.roots[o[i]];
@@ -1769,8 +1821,9 @@ int trace_enqueue(mpmc_ctx* h, uint64_t seed, int nsamples, int first, int nb, i
                 // r = b - (A Z) D with D = H^{-1} U^H b; the sample adds b^H Z D
                 launch_proj_coef(h->k, nb, h->d_pair, h->d_invd, h->d_Hinv, h->G1, h->G2, h->D, h->D32, h->xz,
                                  h->stream);
+                begin_chain(h, ns, 0x7072u);
                 launch_rank_update(proj_math(h), h->storage, h->g.V, nb, h->Wb, h->k, h->D, h->D32, -1.0, nullptr,
-                                   ns, ws.r, h->stream);
+                                   ns, ws.r, h->stream, next_salt(h));
                 LAUNCHED(2);
                 if (int rc = chain_trace(h, ws, h->polys[l], ns, ws.r, ws.acc_hi, &c_hi)) return rc;
             } else {
@@ -1994,8 +2047,8 @@ int mpmc_set_links(mpmc_handle h, const double* links) {
     LAUNCHED(1);
     h->proj_ready = false;   // A Z changes with the links
     if (h->links32) {
-        launch_links(ST_F32, h->g.V, h->io, h->links32, h->stream);
-        launch_links_expanded(h->g.V, h->io, h->links_ex, h->stream);
+        launch_links(ST_F32, h->g.V, h->io, h->links32, h->stream, h->kappa);
+        launch_links_expanded(h->g.V, h->io, h->links_ex, h->stream, h->kappa);
         LAUNCHED(2);
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -2033,7 +2086,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     const bool prof = h->prof;
     h->prof = false;
     const int nbs[] = {16, 32, 64, 128, 256, 512, 1024};
-    const int bxs[] = {32, 64};
+    const int bxs[] = {16, 32, 64};
     const int sls[] = {1, 2};
     const NoiseSpec ns{0x5eedULL, 0, 0};
     int rc = MPMC_OK;
@@ -2050,7 +2103,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                     a.out = ws.w[j % 2];
                     a.dot = cls == 0;
                     setc(a.alpha, 0.5);
-                    a.kappa = h->kappa;
+                    a.kappa = kap(h, h->storage);
                     setc(a.dot_w, 1.0);
                     a.acc = ws.acc_hi;
                     if (int r = step_launch(h, ws, a, ns)) return r;
@@ -2063,7 +2116,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                     setc(o.alpha, 0.5);
                     setc(o.beta, 0.25);
                     setc(o.gamma, 0.125);
-                    o.kappa = h->kappa;
+                    o.kappa = kap(h, h->storage);
                     if (int r = outer_launch(h, ws, o, ns)) return r;
                 }
             }
@@ -2185,10 +2238,13 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         const int shapes[][3] = {{bR, bbx, bsl}, {1, 32, 2}, {1, 64, 1}, {2, 32, 1}};
         for (const auto& sh : shapes)
             for (int fm : {0, 1, 3, 5, 7})
-                for (int sm : {0, 7}) {
+                for (int sm : {0, 7, 23}) {
                     if (sm && !fsw) continue;
                     if (fm == 7 && sh != shapes[0]) continue;   // no site-parallel step left to shape
-                    const int f = fm & user_fast, sw = (sm & f & user_sweep) | (bsweep & 8);
+                    // the links-staged t-sweep (bit 16) only with the shape found in phase 1
+                    if (sm == 23 && (sh != shapes[0] || !(user_sweep & 16) || !(fm & 7))) continue;
+                    const int f = fm & user_fast;
+                    const int sw = (sm & f & user_sweep) | (sm & user_sweep & 16) | (bsweep & 8);
                     cand.push_back({f, sw, sh[0], sh[1], sh[2]});
                 }
         double tbest = INFINITY;
@@ -2446,6 +2502,10 @@ struct mpmc_batch {
     cudaGraphExec_t exec = nullptr;
     size_t nodes = 0;
     long long launches = 0;
+    // stochastic rounding of BF16 chain stores: salt of the current chain (from its noise block and
+    // polynomial) and the position of the next step in it, so that a call's random bits depend on
+    // what it computes, not on the handle's history
+    uint32_t sr_base = 0, sr_step = 0;
     uint64_t key_seed = 0;
     int key_n = -1, key_first = -1;
     std::vector<unsigned long long> key_gen;

@@ -88,7 +88,7 @@ template <> struct DTy<float> { using type = float2; };
 // out[site][e][c] = base[site][e][c] + sign * sum_i Y[site][e][i] D[i][c]; base = noise when null.
 template <class S, class T>
 __global__ void k_rank_update(int V, int nb, const T* __restrict__ Y, int k, const typename DTy<T>::type* __restrict__ D,
-                              T sign, const S* base, NoiseKey nk, S* out) {
+                              T sign, const S* base, NoiseKey nk, S* out, uint32_t salt) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)V * nb) return;
     const int site = (int)(idx / nb), c = (int)(idx % nb);
@@ -115,20 +115,23 @@ __global__ void k_rank_update(int V, int nb, const T* __restrict__ Y, int k, con
             cmac(acc[e], cplx<T>{q[0], q[1]}, d);
         }
     }
+    using MS = typename Math<S>::T;   // arithmetic type of the storage format
     S* po = out + ((size_t)site * 12 * nb + c) * 2;
 #pragma unroll
-    for (int e = 0; e < 12; ++e) st(po + (size_t)e * nb * 2, acc[e]);
+    for (int e = 0; e < 12; ++e)   // BF16: stochastic rounding (zero-mean errors), see device.cuh
+        st_sr(po + (size_t)e * nb * 2, cplx<MS>{(MS)acc[e].re, (MS)acc[e].im},
+              sr_bits(sr_seed(salt, (uint32_t)site, (uint32_t)c), e));
 }
 
 // vector-major [k][V*12] -> block layout [site][e][k]
-template <class T>
-__global__ void k_vec_to_block(int V, int k, const T* __restrict__ src, T* dst) {
+template <class TS, class TD>
+__global__ void k_vec_to_block(int V, int k, const TS* __restrict__ src, TD* dst) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // over V*12*k (block order)
     if (idx >= (size_t)V * 12 * k) return;
     const size_t row = idx / k;
     const int i = (int)(idx % k);
-    dst[idx * 2] = src[((size_t)i * V * 12 + row) * 2];
-    dst[idx * 2 + 1] = src[((size_t)i * V * 12 + row) * 2 + 1];
+    dst[idx * 2] = (TD)src[((size_t)i * V * 12 + row) * 2];
+    dst[idx * 2 + 1] = (TD)src[((size_t)i * V * 12 + row) * 2 + 1];
 }
 
 // Per column c of two blocks X, Y ([site][e][nb], FP64): partial sums of |x|^2, |y|^2, x^H y.
@@ -202,19 +205,27 @@ void launch_proj_coef(int k, int nb, const int* pair, const double2* inv_d, cons
 // math: precision of Y and D (ST_F64 -> double Y, D64; otherwise float Y, D32); storage: of base/out
 void launch_rank_update(int math, int storage, int V, int nb, const void* Y, int k, const double2* D64,
                         const float2* D32, double sign, const void* base, const NoiseSpec& ns, void* out,
-                        cudaStream_t s) {
+                        cudaStream_t s, uint32_t salt) {
     const size_t n = (size_t)V * nb;
     const NoiseKey nk = key_of(ns);
-    if (math == ST_F64) {
+    if (math == ST_F64 && storage == ST_F64) {
         k_rank_update<double, double><<<nblk(n, 128), 128, 0, s>>>(V, nb, (const double*)Y, k, D64, sign,
-                                                                (const double*)base, nk, (double*)out);
+                                                                (const double*)base, nk, (double*)out, salt);
+    } else if (math == ST_F64 && storage == ST_F32) {
+        // FP64 projection of a reduced-precision block: the sum is formed in FP64 and rounded once
+        k_rank_update<float, double><<<nblk(n, 128), 128, 0, s>>>(V, nb, (const double*)Y, k, D64, sign,
+                                                               (const float*)base, nk, (float*)out, salt);
+    } else if (math == ST_F64) {
+        k_rank_update<__nv_bfloat16, double><<<nblk(n, 128), 128, 0, s>>>(V, nb, (const double*)Y, k, D64, sign,
+                                                                       (const __nv_bfloat16*)base, nk,
+                                                                       (__nv_bfloat16*)out, salt);
     } else if (storage == ST_F32) {
         k_rank_update<float, float><<<nblk(n, 128), 128, 0, s>>>(V, nb, (const float*)Y, k, D32, (float)sign,
-                                                              (const float*)base, nk, (float*)out);
+                                                              (const float*)base, nk, (float*)out, salt);
     } else {
         k_rank_update<__nv_bfloat16, float><<<nblk(n, 128), 128, 0, s>>>(V, nb, (const float*)Y, k, D32, (float)sign,
                                                                       (const __nv_bfloat16*)base, nk,
-                                                                      (__nv_bfloat16*)out);
+                                                                      (__nv_bfloat16*)out, salt);
     }
 }
 
@@ -224,10 +235,15 @@ void launch_col_stats(int V, int nb, const double* X, const double* Y, double* p
     k_col_stats_reduce<<<nblk(nb, 64), 64, 0, s>>>(nb, nsplit, part, out);
 }
 
-void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s) {
+void launch_vec_to_block(int math, int V, int k, const void* src, void* dst, cudaStream_t s, int src_storage) {
     const size_t n = (size_t)V * 12 * k;
-    if (math == ST_F64) k_vec_to_block<double><<<nblk(n, 256), 256, 0, s>>>(V, k, (const double*)src, (double*)dst);
-    else k_vec_to_block<float><<<nblk(n, 256), 256, 0, s>>>(V, k, (const float*)src, (float*)dst);
+    if (src_storage < 0) src_storage = math;
+    if (math == ST_F64 && src_storage == ST_F64)
+        k_vec_to_block<double, double><<<nblk(n, 256), 256, 0, s>>>(V, k, (const double*)src, (double*)dst);
+    else if (math == ST_F64)   // vectors held in FP32 (exactly), widened to FP64
+        k_vec_to_block<float, double><<<nblk(n, 256), 256, 0, s>>>(V, k, (const float*)src, (double*)dst);
+    else
+        k_vec_to_block<float, float><<<nblk(n, 256), 256, 0, s>>>(V, k, (const float*)src, (float*)dst);
 }
 
 }  // namespace mpmc

@@ -56,6 +56,7 @@ template <> struct VecIO<float, 1> {
     static __device__ __forceinline__ void st(float* p, const cplx<float> (&v)[1]) {
         *reinterpret_cast<float2*>(p) = make_float2(v[0].re, v[0].im);
     }
+    static __device__ __forceinline__ void st_sr(float* p, const cplx<float> (&v)[1], const uint32_t (&)[1]) { st(p, v); }
 };
 template <> struct VecIO<float, 2> {
     static __device__ __forceinline__ void ld(const float* p, cplx<float> (&v)[2]) {
@@ -66,6 +67,7 @@ template <> struct VecIO<float, 2> {
     static __device__ __forceinline__ void st(float* p, const cplx<float> (&v)[2]) {
         *reinterpret_cast<float4*>(p) = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
     }
+    static __device__ __forceinline__ void st_sr(float* p, const cplx<float> (&v)[2], const uint32_t (&)[2]) { st(p, v); }
 };
 template <> struct VecIO<double, 1> {
     static __device__ __forceinline__ void ld(const double* p, cplx<double> (&v)[1]) {
@@ -75,6 +77,7 @@ template <> struct VecIO<double, 1> {
     static __device__ __forceinline__ void st(double* p, const cplx<double> (&v)[1]) {
         *reinterpret_cast<double2*>(p) = make_double2(v[0].re, v[0].im);
     }
+    static __device__ __forceinline__ void st_sr(double* p, const cplx<double> (&v)[1], const uint32_t (&)[1]) { st(p, v); }
 };
 template <> struct VecIO<double, 2> {
     static __device__ __forceinline__ void ld(const double* p, cplx<double> (&v)[2]) {
@@ -86,6 +89,7 @@ template <> struct VecIO<double, 2> {
         reinterpret_cast<double2*>(p)[0] = make_double2(v[0].re, v[0].im);
         reinterpret_cast<double2*>(p)[1] = make_double2(v[1].re, v[1].im);
     }
+    static __device__ __forceinline__ void st_sr(double* p, const cplx<double> (&v)[2], const uint32_t (&)[2]) { st(p, v); }
 };
 template <> struct VecIO<__nv_bfloat16, 1> {
     static __device__ __forceinline__ void ld(const __nv_bfloat16* p, cplx<float> (&v)[1]) {
@@ -94,6 +98,9 @@ template <> struct VecIO<__nv_bfloat16, 1> {
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, const cplx<float> (&v)[1]) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v[0].re, v[0].im);
+    }
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, const cplx<float> (&v)[1], const uint32_t (&rb)[1]) {
+        *reinterpret_cast<uint32_t*>(p) = bf16x2_sr(v[0].re, v[0].im, rb[0]);
     }
 };
 template <> struct VecIO<__nv_bfloat16, 2> {
@@ -109,6 +116,12 @@ template <> struct VecIO<__nv_bfloat16, 2> {
         uint2 x;
         x.x = *reinterpret_cast<uint32_t*>(&a);
         x.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = x;
+    }
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, const cplx<float> (&v)[2], const uint32_t (&rb)[2]) {
+        uint2 x;
+        x.x = bf16x2_sr(v[0].re, v[0].im, rb[0]);
+        x.y = bf16x2_sr(v[1].re, v[1].im, rb[1]);
         *reinterpret_cast<uint2*>(p) = x;
     }
 };
@@ -225,47 +238,27 @@ __device__ __forceinline__ void hopping_r(const Lattice& L, const T* __restrict_
     src.get(nb.bwd[3], col0, psi); load_link(U, nb.bwd[3], 3, u); hop_r<3, false, true>(psi, u, sb, acc);
 }
 
-// A coefficient c as the kernels of one arithmetic apply it: FP64 kernels use c;
-// FP32 kernels use the pair hi = fl32(c), lo = fl32(c - hi) and apply both, so the
-// coefficient enters to ~1e-15 relative and FP32 chains apply the same matrix and
-// polynomial as FP64 ones (only the arithmetic rounds, not the coefficients).
 template <class T> struct Coef;
 template <> struct Coef<float> {
-    static constexpr bool split = true;
     static __device__ __forceinline__ cplx<float> get(const double (&)[2], const float (&f)[2]) { return {f[0], f[1]}; }
     static __device__ __forceinline__ float real(double, float f) { return f; }
 };
 template <> struct Coef<double> {
-    static constexpr bool split = false;
     static __device__ __forceinline__ cplx<double> get(const double (&d)[2], const float (&)[2]) { return {d[0], d[1]}; }
     static __device__ __forceinline__ double real(double d, float) { return d; }
 };
 
-// t = own - kappa * hw  (A applied): kappa = kh (+ kl when SPLIT)
-template <bool SPLIT, class T>
-__device__ __forceinline__ cplx<T> apply_A_elem(cplx<T> own, cplx<T> hw, T kh, T kl) {
-    cplx<T> t{fma(-kh, hw.re, own.re), fma(-kh, hw.im, own.im)};
-    if (SPLIT) {
-        t.re = fma(-kl, hw.re, t.re);
-        t.im = fma(-kl, hw.im, t.im);
-    }
-    return t;
+// t = own - kappa * hw  (A applied), then out = own - alpha * t
+template <class T>
+__device__ __forceinline__ cplx<T> apply_A_elem(cplx<T> own, cplx<T> hw, T kappa) {
+    return {fma(-kappa, hw.re, own.re), fma(-kappa, hw.im, own.im)};
 }
-// own - alpha * t: alpha = ah (+ al when SPLIT)
-template <bool SPLIT, class T>
-__device__ __forceinline__ cplx<T> minus_alpha(cplx<T> own, cplx<T> ah, cplx<T> al, cplx<T> t) {
+template <class T>
+__device__ __forceinline__ cplx<T> minus_alpha(cplx<T> own, cplx<T> alpha, cplx<T> t) {
     cplx<T> o = own;
-    cmac(o, cplx<T>{-ah.re, -ah.im}, t);
-    if (SPLIT) cmac(o, cplx<T>{-al.re, -al.im}, t);
+    cmac(o, cplx<T>{-alpha.re, -alpha.im}, t);
     return o;
 }
-// acc += c * v: c = ch (+ cl when SPLIT)
-template <bool SPLIT, class T>
-__device__ __forceinline__ void cmac2(cplx<T>& acc, cplx<T> ch, cplx<T> cl, cplx<T> v) {
-    cmac(acc, ch, v);
-    if (SPLIT) cmac(acc, cl, v);
-}
-template <class T> __device__ __forceinline__ cplx<T> lo_of(const float (&l)[2]) { return {T(l[0]), T(l[1])}; }
 
 // Reduce R per-thread partial dots over threadIdx.y in fixed order (FP64),
 // then acc[blockIdx.x][col] += w * sum.
@@ -300,14 +293,12 @@ template <class S, int R, bool NOISE_IN, bool DOT, int YMODE>
 __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
                                               int nb, NoiseKey nk, int sl) {
     using T = typename Math<S>::T;
-    constexpr bool SP = Coef<T>::split;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf);
     const bool op_only = a.op_only;
     const cplx<T> cya = Coef<T>::get(a.ya, a.yaf), cyb = Coef<T>::get(a.yb, a.ybf);
-    const cplx<T> cyal = lo_of<T>(a.yal), cybl = lo_of<T>(a.ybl);
     cplx<T> dsum[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dsum[r] = cz<T>();
@@ -328,35 +319,41 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, Lattice L, const typen
         const size_t off = ((size_t)site * 12 * nb + col0) * 2;
         S* po = reinterpret_cast<S*>(a.out) + off;
         S* py = reinterpret_cast<S*>(a.y) + off;
-        uint32_t wq[R];
+        uint32_t wq[R], hsr[R], rb[R], rby[R];
         if (DOT)
 #pragma unroll
             for (int r = 0; r < R; ++r) wq[r] = z4_word(nk, site, col0 + r);
 #pragma unroll
+        for (int r = 0; r < R; ++r) hsr[r] = sr_seed(a.salt, (uint32_t)site, (uint32_t)(col0 + r));
+#pragma unroll
         for (int e = 0; e < 12; ++e) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                rb[r] = sr_bits(hsr[r], e);
+                rby[r] = sr_bits(hsr[r], 12 + e);
+            }
             cplx<T> out[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const cplx<T> t = apply_A_elem<SP>(own[e][r], hw[e][r], kap, kapl);
-                out[r] = op_only ? t : minus_alpha<SP>(own[e][r], cal, call, t);
+                const cplx<T> t = apply_A_elem(own[e][r], hw[e][r], kap);
+                out[r] = op_only ? t : minus_alpha(own[e][r], cal, t);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), out[r]);
             }
-            VecIO<S, R>::st(po + (size_t)e * nb * 2, out);
+            VecIO<S, R>::st_sr(po + (size_t)e * nb * 2, out, rb);
             if (YMODE == 1) {
                 cplx<T> yv[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     yv[r] = cmul_f(cya, own[e][r]);
-                    if (SP) cmac(yv[r], cyal, own[e][r]);
-                    cmac2<SP>(yv[r], cyb, cybl, out[r]);
+                    cmac(yv[r], cyb, out[r]);
                 }
-                VecIO<S, R>::st(py + (size_t)e * nb * 2, yv);
+                VecIO<S, R>::st_sr(py + (size_t)e * nb * 2, yv, rby);
             } else if (YMODE == 2) {
                 cplx<T> yv[R];
                 VecIO<S, R>::ld(py + (size_t)e * nb * 2, yv);
 #pragma unroll
-                for (int r = 0; r < R; ++r) cmac2<SP>(yv[r], cyb, cybl, out[r]);
-                VecIO<S, R>::st(py + (size_t)e * nb * 2, yv);
+                for (int r = 0; r < R; ++r) cmac(yv[r], cyb, out[r]);
+                VecIO<S, R>::st_sr(py + (size_t)e * nb * 2, yv, rby);
             }
         }
     }
@@ -368,13 +365,11 @@ template <class S, int R, bool DOT>
 __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typename Math<S>::T* __restrict__ U,
                                                int nb, NoiseKey nk, int sl) {
     using T = typename Math<S>::T;
-    constexpr bool SP = Coef<T>::split;
     const int col0 = (blockIdx.y * blockDim.x + threadIdx.x) * R;
     const bool colok = col0 < nb;
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf);
     const cplx<T> cb = Coef<T>::get(a.beta, a.betaf), cg = Coef<T>::get(a.gamma, a.gammaf);
-    const cplx<T> cbl = lo_of<T>(a.betal), cgl = lo_of<T>(a.gammal);
     cplx<T> dsum[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dsum[r] = cz<T>();
@@ -390,25 +385,32 @@ __global__ void __launch_bounds__(256) k_outer(OuterArgs a, Lattice L, const typ
         const S* pw = reinterpret_cast<const S*>(a.w) + off;
         S* pwo = reinterpret_cast<S*>(a.wout) + off;
         S* py = reinterpret_cast<S*>(a.y) + off;
-        uint32_t wq[R];
+        uint32_t wq[R], hsr[R], rb[R], rby[R];
         if (DOT)
 #pragma unroll
             for (int r = 0; r < R; ++r) wq[r] = z4_word(nk, site, col0 + r);
 #pragma unroll
+        for (int r = 0; r < R; ++r) hsr[r] = sr_seed(a.salt, (uint32_t)site, (uint32_t)(col0 + r));
+#pragma unroll
         for (int e = 0; e < 12; ++e) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                rb[r] = sr_bits(hsr[r], e);
+                rby[r] = sr_bits(hsr[r], 12 + e);
+            }
             cplx<T> wv[R], yv[R];
             VecIO<S, R>::ld(pw + (size_t)e * nb * 2, wv);
             VecIO<S, R>::ld(py + (size_t)e * nb * 2, yv);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const cplx<T> t = minus_alpha<SP>(own[e][r], cal, call, apply_A_elem<SP>(own[e][r], hw[e][r], kap, kapl));
-                const cplx<T> wn = minus_alpha<SP>(wv[r], cb, cbl, wv[r] - t);
+                const cplx<T> t = minus_alpha(own[e][r], cal, apply_A_elem(own[e][r], hw[e][r], kap));
+                const cplx<T> wn = minus_alpha(wv[r], cb, wv[r] - t);
                 wv[r] = wn;
-                cmac2<SP>(yv[r], cg, cgl, wn);
+                cmac(yv[r], cg, wn);
                 if (DOT) dsum[r] = dsum[r] + z4_conj_mul<T>(wq[r] >> (2 * e), yv[r]);
             }
-            VecIO<S, R>::st(pwo + (size_t)e * nb * 2, wv);
-            VecIO<S, R>::st(py + (size_t)e * nb * 2, yv);
+            VecIO<S, R>::st_sr(pwo + (size_t)e * nb * 2, wv, rb);
+            VecIO<S, R>::st_sr(py + (size_t)e * nb * 2, yv, rby);
         }
     }
     if (DOT) cta_dot_r<T, R>(dsum, col0, colok, nb, a.dot_w, a.acc);

@@ -14,14 +14,14 @@ __global__ void k_noise_words(int V, int nb, NoiseKey nk, uint32_t* __restrict__
     out[idx] = z4_word(nk, site, col);
 }
 
-__global__ void k_links_expanded(int V, const double* __restrict__ src, float4* __restrict__ dst) {
+__global__ void k_links_expanded(int V, const double* __restrict__ src, double scale, float4* __restrict__ dst) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu, i)
     if (idx >= (size_t)V * 36) return;
     const int i = (int)(idx % 9);
     const int mu = (int)((idx / 9) % 4);
     const size_t site = idx / 36;
     const double* p = src + (((size_t)mu * V + site) * 9 + i) * 2;
-    const float re = (float)p[0], im = (float)p[1];
+    const float re = (float)(scale * p[0]), im = (float)(scale * p[1]);
     dst[idx] = make_float4(re, re, im, im);
 }
 
@@ -88,9 +88,9 @@ void launch_noise_words(const Geom& g, int nb, const NoiseSpec& ns, uint32_t* wo
     k_noise_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.V, nb, nk, words);
 }
 
-void launch_links_expanded(int V, const double* src, float4* dst, cudaStream_t s) {
+void launch_links_expanded(int V, const double* src, float4* dst, cudaStream_t s, double scale) {
     const size_t n = (size_t)V * 36;
-    k_links_expanded<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, src, dst);
+    k_links_expanded<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, src, scale, dst);
 }
 
 }  // namespace mpmc

@@ -36,6 +36,7 @@ template <> struct Row<float> {
     static __device__ __forceinline__ float2 ld(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
     static __device__ __forceinline__ float2 ld_rw(const float* p) { return *reinterpret_cast<const float2*>(p); }
     static __device__ __forceinline__ void st(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+    static __device__ __forceinline__ void st_sr(float* p, float2 v, uint32_t) { st(p, v); }
 };
 template <> struct Row<__nv_bfloat16> {
     static __device__ __forceinline__ float2 cvt(uint32_t w) {
@@ -49,6 +50,10 @@ template <> struct Row<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
+    // stochastic rounding (zero-mean errors) for the chain vectors
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16* p, float2 v, uint32_t rb) {
+        *reinterpret_cast<uint32_t*>(p) = bf16x2_sr(v.x, v.y, rb);
     }
 };
 
@@ -197,17 +202,6 @@ __device__ __forceinline__ float2 cmac2(float2 acc, float2 c, float2 v) {
     acc.y = fmaf(c.y, v.x, acc.y);
     return acc;
 }
-// The same with a coefficient given as an FP32 hi + lo pair (applied to ~1e-15 relative):
-// t = own - kappa hw;  own - alpha t;  acc + c v
-__device__ __forceinline__ float2 apply_A2(float2 own, float2 hw, float2 mkh, float2 mkl) {
-    return fma2(mkl, hw, fma2(mkh, hw, own));
-}
-__device__ __forceinline__ float2 minus_alpha2(float2 own, float2 ah, float2 al, float2 t) {
-    return minus_alpha2(minus_alpha2(own, ah, t), al, t);
-}
-__device__ __forceinline__ float2 cmac2(float2 acc, float2 ch, float2 cl, float2 v) {
-    return cmac2(cmac2(acc, ch, v), cl, v);
-}
 
 // (cr, cr, ci, ci) of conj(i^q) and i^q, for the shared tables
 __device__ __forceinline__ float4 z4_conj_entry(int q) {
@@ -233,8 +227,8 @@ __global__ void __launch_bounds__(256) k_fast(const FastArgs a) {
     __syncthreads();
     const int col = blockIdx.y * TW + threadIdx.x;
     float dre = 0.f, dim = 0.f;
-    const float2 al = make_float2(a.alpha[0], a.alpha[1]), all = make_float2(a.alpha_lo[0], a.alpha_lo[1]);
-    const float2 mk = make_float2(-a.kappa, -a.kappa), mkl = make_float2(-a.kappa_lo, -a.kappa_lo);
+    const float2 al = make_float2(a.alpha[0], a.alpha[1]);
+    const float2 mk = make_float2(-a.kappa, -a.kappa);
     for (int it = 0; it < a.sl; ++it) {
         const int site = (blockIdx.x * a.sl + it) * SB + threadIdx.y;
         if (site >= a.V) break;
@@ -250,25 +244,25 @@ __global__ void __launch_bounds__(256) k_fast(const FastArgs a) {
         if (DOT || NOISE) word = __ldg(a.words + (size_t)site * NB + col);
         const size_t off = ((size_t)site * 12 * NB + col) * 2;
         const S* pin = NOISE ? nullptr : reinterpret_cast<const S*>(a.in) + off;
+        const uint32_t hsr = sr_seed(a.salt, (uint32_t)site, (uint32_t)col);
         float2 dA = make_float2(0.f, 0.f), dB = make_float2(0.f, 0.f);
 #pragma unroll
         for (int e = 0; e < 12; ++e) {
             const float2 own = NOISE ? zval[(word >> (2 * e)) & 3u] : Row<S>::ld(pin + (size_t)e * NB * 2);
-            const float2 t = apply_A2(own, hw[e], mk, mkl);        // own - kappa H own
+            const float2 t = fma2(mk, hw[e], own);                 // own - kappa H own
             float2 v;
             if (!OUTER) {
-                v = minus_alpha2(own, al, all, t);                 // (I - A/theta) own
-                Row<S>::st(reinterpret_cast<S*>(a.out) + off + (size_t)e * NB * 2, v);
+                v = minus_alpha2(own, al, t);                      // (I - A/theta) own
+                Row<S>::st_sr(reinterpret_cast<S*>(a.out) + off + (size_t)e * NB * 2, v, sr_bits(hsr, e));
             } else {
-                const float2 tt = minus_alpha2(own, al, all, t);   // pi_in(A) w
+                const float2 tt = minus_alpha2(own, al, t);        // pi_in(A) w
                 const size_t oe = off + (size_t)e * NB * 2;
                 const float2 wv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.w) + oe);
                 float2 yv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.y) + oe);
-                const float2 wn = minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]),
-                                               make_float2(a.beta_lo[0], a.beta_lo[1]), sub2(wv, tt));
-                yv = cmac2(yv, make_float2(a.gamma[0], a.gamma[1]), make_float2(a.gamma_lo[0], a.gamma_lo[1]), wn);
-                Row<S>::st(reinterpret_cast<S*>(a.out) + oe, wn);
-                Row<S>::st(reinterpret_cast<S*>(a.y) + oe, yv);
+                const float2 wn = minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]), sub2(wv, tt));
+                yv = cmac2(yv, make_float2(a.gamma[0], a.gamma[1]), wn);
+                Row<S>::st_sr(reinterpret_cast<S*>(a.out) + oe, wn, sr_bits(hsr, e));
+                Row<S>::st_sr(reinterpret_cast<S*>(a.y) + oe, yv, sr_bits(hsr, 12 + e));
                 v = yv;
             }
             if (DOT) {

@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(LSM ? 128 : 8 * (NB < 32 ? NB : 32), LSM ? 3 :
     if (tid == 0)
         for (int rel = 0; rel < RING && rel < nrel; ++rel) issue(rel);
 
-    const float2 al = make_float2(a.alpha[0], a.alpha[1]), all = make_float2(a.alpha_lo[0], a.alpha_lo[1]);
-    const float2 mk = make_float2(-a.kappa, -a.kappa), mkl = make_float2(-a.kappa_lo, -a.kappa_lo);
+    const float2 al = make_float2(a.alpha[0], a.alpha[1]);
+    const float2 mk = make_float2(-a.kappa, -a.kappa);
     const long long deadline = clock64() + a.wait_limit;
     double dre = 0.0, dim = 0.0;
     float fre = 0.f, fim = 0.f;   // FP32 partial of the noise dot, moved to FP64 every 4 planes
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(LSM ? 128 : 8 * (NB < 32 ? NB : 32), LSM ? 3 :
             srow(P0, sib, p);   // own row
 
             const size_t off = ((size_t)site * 12 * NB + col) * 2;
+            const uint32_t hsr = sr_seed(a.salt, (uint32_t)site, (uint32_t)col);
             uint32_t word = 0;
             if (DOT) word = __ldg(a.words + (size_t)site * NB + col);
             float2 dA = make_float2(0.f, 0.f), dB = make_float2(0.f, 0.f);
@@ -247,22 +248,20 @@ __global__ void __launch_bounds__(LSM ? 128 : 8 * (NB < 32 ? NB : 32), LSM ? 3 :
             for (int e = 0; e < 12; ++e) {
                 const float2 hw = e < 6 ? up[e] : make_float2(lr[e - 6].x - lj[e - 6].y, lr[e - 6].y + lj[e - 6].x);
                 const float2 own = p[e];
-                const float2 tt = fast::apply_A2(own, hw, mk, mkl);
+                const float2 tt = fma2(mk, hw, own);
                 float2 v;
                 if (!OUTER) {
-                    v = fast::minus_alpha2(own, al, all, tt);
-                    Row<S>::st(reinterpret_cast<S*>(a.out) + off + (size_t)e * NB * 2, v);
+                    v = fast::minus_alpha2(own, al, tt);
+                    Row<S>::st_sr(reinterpret_cast<S*>(a.out) + off + (size_t)e * NB * 2, v, sr_bits(hsr, e));
                 } else {
-                    const float2 pa = fast::minus_alpha2(own, al, all, tt);
+                    const float2 pa = fast::minus_alpha2(own, al, tt);
                     const size_t oe = off + (size_t)e * NB * 2;
                     const float2 wv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.w) + oe);
                     float2 yv = Row<S>::ld_rw(reinterpret_cast<const S*>(a.y) + oe);
-                    const float2 wn = fast::minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]),
-                                                         make_float2(a.beta_lo[0], a.beta_lo[1]), sub2(wv, pa));
-                    yv = fast::cmac2(yv, make_float2(a.gamma[0], a.gamma[1]),
-                                     make_float2(a.gamma_lo[0], a.gamma_lo[1]), wn);
-                    Row<S>::st(reinterpret_cast<S*>(a.out) + oe, wn);
-                    Row<S>::st(reinterpret_cast<S*>(a.y) + oe, yv);
+                    const float2 wn = fast::minus_alpha2(wv, make_float2(a.beta[0], a.beta[1]), sub2(wv, pa));
+                    yv = fast::cmac2(yv, make_float2(a.gamma[0], a.gamma[1]), wn);
+                    Row<S>::st_sr(reinterpret_cast<S*>(a.out) + oe, wn, sr_bits(hsr, e));
+                    Row<S>::st_sr(reinterpret_cast<S*>(a.y) + oe, yv, sr_bits(hsr, 12 + e));
                     v = yv;
                 }
                 if (DOT) {

@@ -93,9 +93,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
     if (threadIdx.x == 0)
         for (int rel = 0; rel < SWEEP_RING && rel < nrel; ++rel) issue(rel);
 
-    constexpr bool SP = Coef<T>::split;
-    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf), call = lo_of<T>(a.alphal);
-    const T kap = Coef<T>::real(a.kappa, a.kappaf), kapl = T(a.kappal);
+    const cplx<T> cal = Coef<T>::get(a.alpha, a.alphaf);
+    const T kap = Coef<T>::real(a.kappa, a.kappaf);
     const long long deadline = clock64() + SWEEP_TIMEOUT;
     double dre = 0.0, dim = 0.0;
 
@@ -144,37 +143,36 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
             srow(P0, warp, own);
 
             const size_t off = ((size_t)site * 12 * nb + col) * 2;
+            const uint32_t hsr = sr_seed(a.salt, (uint32_t)site, (uint32_t)col);
             uint32_t wq = 0;
             if (DOT) wq = z4_word(nk, site, col);
             cplx<T> dsum = cz<T>();
             if constexpr (!OUTER) {
                 const cplx<T> cya = Coef<T>::get(a.ya, a.yaf), cyb = Coef<T>::get(a.yb, a.ybf);
-                const cplx<T> cyal = lo_of<T>(a.yal), cybl = lo_of<T>(a.ybl);
                 S* po = reinterpret_cast<S*>(a.out) + off;
                 S* py = reinterpret_cast<S*>(a.y) + off;
 #pragma unroll
                 for (int e = 0; e < 12; ++e) {
                     cplx<T> out[1];
-                    const cplx<T> tt = apply_A_elem<SP>(own[e][0], acc[e][0], kap, kapl);
-                    out[0] = a.op_only ? tt : minus_alpha<SP>(own[e][0], cal, call, tt);
+                    const cplx<T> tt = apply_A_elem(own[e][0], acc[e][0], kap);
+                    out[0] = a.op_only ? tt : minus_alpha(own[e][0], cal, tt);
                     if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), out[0]);
-                    VecIO<S, 1>::st(po + (size_t)e * nb * 2, out);
+                    const uint32_t rb[1] = {sr_bits(hsr, e)}, rby[1] = {sr_bits(hsr, 12 + e)};
+                    VecIO<S, 1>::st_sr(po + (size_t)e * nb * 2, out, rb);
                     if (YMODE == 1) {
                         cplx<T> yv[1];
                         yv[0] = cmul_f(cya, own[e][0]);
-                        if (SP) cmac(yv[0], cyal, own[e][0]);
-                        cmac2<SP>(yv[0], cyb, cybl, out[0]);
-                        VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);
+                        cmac(yv[0], cyb, out[0]);
+                        VecIO<S, 1>::st_sr(py + (size_t)e * nb * 2, yv, rby);
                     } else if (YMODE == 2) {
                         cplx<T> yv[1];
                         VecIO<S, 1>::ld(py + (size_t)e * nb * 2, yv);
-                        cmac2<SP>(yv[0], cyb, cybl, out[0]);
-                        VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);
+                        cmac(yv[0], cyb, out[0]);
+                        VecIO<S, 1>::st_sr(py + (size_t)e * nb * 2, yv, rby);
                     }
                 }
             } else {
                 const cplx<T> cb = Coef<T>::get(a.beta, a.betaf), cg = Coef<T>::get(a.gamma, a.gammaf);
-                const cplx<T> cbl = lo_of<T>(a.betal), cgl = lo_of<T>(a.gammal);
                 const S* pw = reinterpret_cast<const S*>(a.w) + off;
                 S* pwo = reinterpret_cast<S*>(a.wout) + off;
                 S* py = reinterpret_cast<S*>(a.y) + off;
@@ -183,13 +181,14 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const __grid_constant__ CUtens
                     cplx<T> wv[1], yv[1];
                     VecIO<S, 1>::ld(pw + (size_t)e * nb * 2, wv);
                     VecIO<S, 1>::ld(py + (size_t)e * nb * 2, yv);
-                    const cplx<T> tt = minus_alpha<SP>(own[e][0], cal, call, apply_A_elem<SP>(own[e][0], acc[e][0], kap, kapl));
-                    const cplx<T> wn = minus_alpha<SP>(wv[0], cb, cbl, wv[0] - tt);
+                    const cplx<T> tt = minus_alpha(own[e][0], cal, apply_A_elem(own[e][0], acc[e][0], kap));
+                    const cplx<T> wn = minus_alpha(wv[0], cb, wv[0] - tt);
                     wv[0] = wn;
-                    cmac2<SP>(yv[0], cg, cgl, wn);
+                    cmac(yv[0], cg, wn);
                     if (DOT) dsum = dsum + z4_conj_mul<T>(wq >> (2 * e), yv[0]);
-                    VecIO<S, 1>::st(pwo + (size_t)e * nb * 2, wv);
-                    VecIO<S, 1>::st(py + (size_t)e * nb * 2, yv);
+                    const uint32_t rb[1] = {sr_bits(hsr, e)}, rby[1] = {sr_bits(hsr, 12 + e)};
+                    VecIO<S, 1>::st_sr(pwo + (size_t)e * nb * 2, wv, rb);
+                    VecIO<S, 1>::st_sr(py + (size_t)e * nb * 2, yv, rby);
                 }
             }
             if (DOT) { dre += (double)dsum.re; dim += (double)dsum.im; }

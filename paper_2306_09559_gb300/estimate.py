@@ -116,6 +116,46 @@ def full_estimate(h_inv, h_lev, eps, seed, pin, colours, ncolours, *, h_probe=No
     return out
 
 
+def precision_corrected_level(h_mix, h64, level, seed, nsamples, ncorr, first=0):
+    """One level estimated in reduced precision with an FP64 correction level.
+
+    The telescoping of Eq. (2) applied across precisions: E[s_64] = E[s_mix] +
+    E[s_64 - s_mix].  The mixed-precision handle draws `nsamples` samples; the
+    FP64 handle (same polynomials and deflation) draws the first `ncorr` of the
+    same noise vectors, and the mean of the paired differences d = s_64 - s_mix
+    is added.  The estimate is then unbiased with respect to the FP64 level
+    whatever the rounding of the mixed path does; d is small, so few FP64
+    samples suffice.  With m the mixed samples and d the differences,
+    Var = Var(m)/N + Var(d)/n + 2 Cov(m, d)/N (the n pairs share their noise with
+    the first n mixed samples).  Returns {"estimate", "se", "mixed", "correction",
+    "var_mixed", "var_diff", "n", "ncorr"}."""
+    if ncorr < 2:
+        raise ValueError("the correction level needs at least two samples")
+    mean_m, _, sm = h_mix.mpmc_trace_level(level, seed, nsamples, first)
+    _, _, s64 = h64.mpmc_trace_level(level, seed, ncorr, first)
+    corr_m = mean_m - np.mean(sm)                  # the level's exact deflation correction
+    d = s64 - sm[:ncorr]
+    m = sm.real
+    var_m = float(np.var(m, ddof=1)) if nsamples > 1 else 0.0
+    var_d = float(np.var(d.real, ddof=1))
+    cov = float(np.cov(m[:ncorr], d.real, ddof=1)[0, 1])
+    var = var_m / nsamples + var_d / ncorr + 2 * cov / nsamples
+    est = complex(np.mean(sm) + corr_m + np.mean(d))
+    return {"estimate": est, "se": math.sqrt(max(var, 0.0)), "mixed": complex(mean_m),
+            "correction": complex(np.mean(d)), "var_mixed": var_m, "var_diff": var_d, "n": int(nsamples),
+            "ncorr": int(ncorr)}
+
+
+def correction_samples(var_mixed, var_diff, cost_mixed, cost_64, nsamples):
+    """Paired FP64 samples for a correction level at the least total cost for the variance
+    of `nsamples` mixed samples (the allocation of Eq. (3) for the two terms):
+    n = N sqrt((V_d / C_64) / (V_m / C_m)), at least 2."""
+    if var_mixed <= 0:
+        return 2
+    n = nsamples * math.sqrt((var_diff / cost_64) / (var_mixed / cost_mixed))
+    return max(2, int(math.ceil(n)))
+
+
 def allocation(variances, costs, eps):
     """Samples per level minimising the cost for total standard error eps (Eq. (3)):
     N_l = eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k); returns (N_l rounded up, cost)."""
@@ -124,3 +164,27 @@ def allocation(variances, costs, eps):
     s = float(np.sum(np.sqrt(v * c)))
     n = np.ceil(np.sqrt(v / c) * s / eps ** 2).astype(np.int64)
     return n, s * s / eps ** 2
+
+
+def choose_degree(h, index, candidates, roots_for, eps, seed, pilot=32, first=0):
+    """The degree of polynomial `index` chosen by the cost model, Eq. (3) (the paper
+    leaves the degrees to the user and names choosing them from the level
+    variances and costs as future work, Sec. 7).
+
+    For each candidate degree d the handle's polynomial `index` is set to the
+    single polynomial roots_for(d); every level is sampled on `pilot` noise vectors
+    (the pilot variances V_l) and priced with its matvecs per sample C_l
+    (mpmc_level_info); the level set costs eps^-2 (sum_l sqrt(V_l C_l))^2 matvecs
+    for total standard error eps.  The handle is left with the cheapest candidate.
+    Returns (best degree, {degree: Eq. (3) cost})."""
+    from . import mpmc as G
+    costs = {}
+    for d in candidates:
+        h.mpmc_set_poly(index, G.SINGLE, roots_for(d), leja=True)
+        _, var, _ = h.mpmc_trace_levels(seed, pilot, first, want_samples=False)
+        C = [h.mpmc_level_info(level)[1] for level in range(h.nlevels)]
+        costs[d] = allocation(var, C, eps)[1]
+    best = min(costs, key=costs.get)
+    h.mpmc_set_poly(index, G.SINGLE, roots_for(best), leja=True)
+    return best, costs
+

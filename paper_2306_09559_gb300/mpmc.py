@@ -21,6 +21,7 @@ MPMC_OK, MPMC_EINVAL, MPMC_ENOMEM, MPMC_ENOTSUP, MPMC_ETIMEOUT, MPMC_ENONFINITE,
 FP64, FP32, BF16S = 0, 1, 2
 SINGLE, COMPOSITE, DEFLATED_COMPOSITE = 0, 1, 2
 MAX_POLYS = 8
+POLY_LEJA, POLY_FP32_COEFS = 1, 2
 MAX_BLOCK = 1024
 
 _LIB = None
@@ -75,6 +76,7 @@ _SIGS = {
     "mpmc_trace_probing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "mpmc_colouring": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_int)]),
+    "mpmc_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "mpmc_trace_probing_colours": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                                   ctypes.c_void_p]),
     "mpmc_trace_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
@@ -214,11 +216,14 @@ class Handle:
     def mpmc_set_block(self, nb):
         self._check(self._L.mpmc_set_block(self._h, int(nb)), "mpmc_set_block")
 
-    def mpmc_set_poly(self, index, kind, roots, outer=None, leja=True):
+    def mpmc_set_poly(self, index, kind, roots, outer=None, leja=True, fp32_coefs=False):
+        """leja: Leja-order the roots; fp32_coefs: round every 1/theta to FP32 (MPMC_POLY_FP32_COEFS),
+        so that handles of every precision apply the same polynomial."""
         r = _c128(roots)
         o = _c128(outer) if outer is not None else None
+        flags = (POLY_LEJA if leja else 0) | (POLY_FP32_COEFS if fp32_coefs else 0)
         rc = self._L.mpmc_set_poly(self._h, int(index), int(kind), _ptr(r), r.size, _ptr(o),
-                                   0 if o is None else o.size, 1 if leja else 0)
+                                   0 if o is None else o.size, flags)
         self._check(rc, "mpmc_set_poly")
         self._set.add(int(index))
 
@@ -464,6 +469,16 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def mpmc_fma_peak(precision):
+    """Measured FMA throughput (TFLOP/s) of the current device's CUDA cores in FP64 or FP32."""
+    L = lib()
+    v = ctypes.c_double()
+    rc = L.mpmc_fma_peak(int(precision), ctypes.byref(v))
+    if rc != MPMC_OK:
+        raise MpmcError(rc, "mpmc_fma_peak: " + L.mpmc_strerror(rc).decode())
+    return v.value
 
 
 def mpmc_colouring(dims, distance):

@@ -154,7 +154,11 @@ def setup(h64, wl, log=None):
 
 
 def configure(h, polys, defl, block=None):
-    """Load a workload's polynomials and deflation into a handle."""
+    """Load a workload's polynomials and deflation into a handle.
+
+    The roots go in with MPMC_POLY_FP32_COEFS: every handle, whatever its
+    precision, then applies the same polynomial (coefficients 1/theta that are
+    FP32 numbers), so mixed-precision and FP64 levels estimate the same traces."""
     if defl is not None:
         Z, lam, pair = defl
         if hasattr(Z, "is_cuda") and Z.is_cuda:
@@ -164,9 +168,9 @@ def configure(h, polys, defl, block=None):
     kinds = {"single": G.SINGLE, "composite": G.COMPOSITE, "deflated_composite": G.DEFLATED_COMPOSITE}
     for i, (kind, r, o) in enumerate(polys):
         if kind == "single":
-            h.mpmc_set_poly(i, G.SINGLE, r, leja=True)
+            h.mpmc_set_poly(i, G.SINGLE, r, leja=True, fp32_coefs=True)
         else:
-            h.mpmc_set_poly(i, kinds[kind], r, o, leja=True)
+            h.mpmc_set_poly(i, kinds[kind], r, o, leja=True, fp32_coefs=True)
     if block:
         h.mpmc_set_block(block)
 

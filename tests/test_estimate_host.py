@@ -54,3 +54,33 @@ def test_allocation_reaches_the_multilevel_cost():
     assert abs(cost - M.multilevel_cost(v, c, eps)) < 1e-9 * cost
     # with N_l samples the total variance sum V_l / N_l is at most eps^2
     assert np.sum(np.array(v) / n) <= eps ** 2 * (1 + 1e-12)
+
+
+def test_precision_corrected_level_is_the_fp64_mean_for_paired_samples():
+    """With fake handles: mixed samples m, FP64 samples f on the same noise; the
+    corrected estimate is mean(m) + mean(f - m)[:n], its variance the three-term
+    formula, and with n = N it equals the FP64 mean exactly."""
+    import numpy as np
+    from paper_2306_09559_gb300 import estimate as E
+
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(40) * 2.0 + 5.0
+    m = f + 0.03 + 1e-3 * rng.standard_normal(40)          # a biased mixed path
+
+    class Fake:
+        def __init__(self, s, corr):
+            self.s, self.corr = s, corr
+
+        def mpmc_trace_level(self, level, seed, n, first):
+            x = self.s[first:first + n].astype(complex)
+            return np.mean(x) + self.corr, np.var(x.real, ddof=1), x
+
+    r = E.precision_corrected_level(Fake(m, 0.5), Fake(f, 0.5), 0, 7, 40, 40)
+    assert abs(r["estimate"] - (np.mean(f) + 0.5)) < 1e-12
+    r = E.precision_corrected_level(Fake(m, 0.5), Fake(f, 0.5), 0, 7, 40, 5)
+    d = f[:5] - m[:5]
+    assert abs(r["estimate"] - (np.mean(m) + 0.5 + np.mean(d))) < 1e-12
+    v = np.var(m, ddof=1) / 40 + np.var(d, ddof=1) / 5 + 2 * np.cov(m[:5], d)[0, 1] / 40
+    assert abs(r["se"] ** 2 - v) < 1e-12
+    assert E.correction_samples(4.0, 1e-6, 1.0, 20.0, 64) == 2
+    assert E.correction_samples(4.0, 4.0, 1.0, 1.0, 64) == 64

@@ -49,3 +49,35 @@ def test_sequential_estimate_on_the_gpu_matches_the_oracle():
         est = np.mean(ref) + M.exact_correction(polys, lv["level"], defl)
         scale = np.mean(np.abs(hi) + np.abs(lo) + np.abs(dt))
         assert abs(lv["estimate"] - est) < 1e-12 * scale, lv
+
+
+def test_choose_degree_minimises_the_eq3_cost():
+    """The degree of p_2 picked from the Eq. (3) cost of pilot runs is the one
+    that minimises that cost computed by the oracle (its own samples of the same
+    noise, its own multilevel_cost), and the library's costs agree with the
+    oracle's to 1e-8."""
+    from conftest import operator
+    from oracle import krylov as K
+    from paper_2306_09559_gb300 import synth
+    from test_gpu_parity import handle, set_polys
+    op = operator((4, 4, 4, 4), "haar", 0, 0.12)
+    b0 = synth.random_unit_vector(op.n, 17)
+    cands = [3, 6, 12, 20, 30]
+    roots = dict(zip(cands + [2], K.gmres_polynomials(op, b0, cands + [2])))
+    p_in = K.gmres_polynomials(op, b0, [5])[0]
+    p_out = K.pp_gmres_roots(op, p_in, b0, m_out=8)[0]
+    eps, seed, pilot = 1.0, 404, 40
+    costs_o = {}
+    for d in cands:
+        polys = [{"kind": "composite", "inner": p_in, "outer": p_out},
+                 {"kind": "single", "roots": roots[d]}, {"kind": "single", "roots": roots[2]}]
+        var = [np.var(M.level_samples(op, polys, l, seed, pilot).real, ddof=1) for l in range(3)]
+        C = [M.spec_matvecs(polys[l]) + (M.spec_matvecs(polys[l + 1]) if l < 2 else 0) for l in range(3)]
+        costs_o[d] = M.multilevel_cost(var, C, eps)
+    with handle((4, 4, 4, 4)) as h:
+        set_polys(h, [{"kind": "composite", "inner": p_in, "outer": p_out},
+                      {"kind": "single", "roots": roots[cands[0]]}, {"kind": "single", "roots": roots[2]}])
+        best, costs = E.choose_degree(h, 1, cands, lambda d: roots[d], eps, seed, pilot=pilot)
+    assert best == min(costs_o, key=costs_o.get)
+    for d in cands:
+        assert abs(costs[d] - costs_o[d]) <= 1e-8 * costs_o[d], d

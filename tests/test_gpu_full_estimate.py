@@ -62,6 +62,9 @@ def _oracle_stop(re, tol, start, step):
 def test_full_estimate_matches_the_oracle_and_dense_lu(prec):
     from test_gpu_parity import set_polys
     op, polys, p_in, lam, Z, pair = _setup()
+    if prec != G.FP64:
+        from conftest import fp32_polys
+        polys = fp32_polys(polys)       # the polynomials an FP32 chain applies, on every side
     defl = M.Deflation(op, Z, lam, pair)
     A = dense(DIMS, "haar", 0, KAPPA)
     lu = sla.lu_factor(A)

@@ -12,7 +12,7 @@ matches the oracle within the paired bound."""
 import numpy as np
 import pytest
 
-from conftest import links, paired_bound
+from conftest import fp32_polys, fp32_resolution, links, paired_bound
 from oracle import mpmc as M
 from paper_2306_09559_gb300 import build
 from paper_2306_09559_gb300 import mpmc as G
@@ -43,6 +43,7 @@ def _handle(prec, Z, lam, pair, polys):
 def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(skip, sweep):
     from test_gpu_parity import small_setup
     op, polys, lam, Z, pair = small_setup()
+    polys = fp32_polys(polys)
     N = 24
     with _handle(G.FP32, Z, lam, pair, polys) as h, _handle(G.FP32, Z, lam, pair, polys) as fresh:
         for hh in (h, fresh):
@@ -60,8 +61,8 @@ def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(skip, swe
     assert np.array_equal(got, ref_gpu)
     defl = M.Deflation(op, Z, lam, pair)
     for level in range(3):
-        ref = M.level_sample_parts(op, polys, level, 3, N, defl)[0]
-        paired_bound(got[level] - ref, ref)
+        ref, hi, lo, _ = M.level_sample_parts(op, polys, level, 3, N, defl)
+        paired_bound(got[level] - ref, ref, resolution=fp32_resolution(hi, lo))
 
 
 def test_wait_options_are_checked():
