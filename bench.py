@@ -449,6 +449,53 @@ def batch_arm(args):
     return 0
 
 
+def correction_levels(wl, polys, m64, v64, x64, mmix, xmix, t64, tmix):
+    """FP64 correction levels for the mixed-precision levels that miss the bias bound.
+
+    A level estimated as mean(s_mix) + mean((s_64 - s_mix)[:n]) is unbiased with respect to
+    FP64 by construction (the telescoping of Eq. (2) across precisions).  n follows the Eq. (3)
+    allocation of the two terms, n = N sqrt((V_d / C_64) / (V_mix / C_mix)), at least 2, with the
+    per-sample costs in the ratio of the measured FP64 and mixed step times.  The corrected
+    estimate is compared with the FP64 one under the bias bound (0.1 SE_64 plus three standard
+    errors of the correction), and the equal-SE speed-up is recomputed with the FP64 samples
+    the corrections cost (at the level's share of the FP64 step time)."""
+    import numpy as np
+    N = wl.nsamples
+    mv = []
+    for kind, r, o in polys:
+        mv.append(len(r) - 1 if kind == "single" else (len(o) - 1) * len(r) + len(r) - 1)
+    level_mv = [mv[l] + (mv[l + 1] if l + 1 < len(mv) else 0) for l in range(len(mv))]
+    share = [x / sum(level_mv) for x in level_mv]
+    out, t_corr, var_total = {"levels": []}, 0.0, 0.0
+    for l in range(len(polys)):
+        dl = (x64[l] - xmix[l]).real
+        se64 = np.sqrt(v64[l] / N)
+        bound = 0.1 * se64 + 3 * np.std(dl, ddof=1) / np.sqrt(N)
+        var_m = float(np.var(xmix[l].real, ddof=1))
+        if abs(np.mean(dl)) <= bound:
+            var_total += var_m
+            continue
+        var_d = float(np.var(dl, ddof=1))
+        n = max(2, int(np.ceil(N * np.sqrt((var_d / t64) / (var_m / tmix))))) if var_m > 0 else 2
+        n = min(n, N)
+        corr_mix = mmix[l] - np.mean(xmix[l])
+        est = np.mean(xmix[l]) + corr_mix + np.mean(x64[l][:n] - xmix[l][:n])
+        cov = float(np.cov(xmix[l].real[:n], dl[:n], ddof=1)[0, 1]) if n > 2 else 0.0
+        var_est = var_m / N + var_d / n + 2 * cov / N
+        dev = abs((est - m64[l]).real)
+        allowed = 0.1 * se64 + 3 * np.sqrt(var_d / n)
+        t_corr += n * t64 * share[l] / N
+        var_total += N * var_est
+        out["levels"].append({"level": l, "mixed_bias_over_se": float(abs(np.mean(dl)) / se64),
+                              "ncorr": n, "var_diff": var_d, "corrected_estimate": [float(est.real), float(est.imag)],
+                              "corrected_minus_fp64_over_se": float(dev / se64),
+                              "corrected_within_bound": bool(dev <= allowed),
+                              "corrected_se": float(np.sqrt(max(var_est, 0.0)))})
+    out["fp64_ms_per_step_for_corrections"] = t_corr
+    out["equal_se_speedup"] = float((t64 * float(np.sum(v64))) / ((tmix + t_corr) * var_total))
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def gpu_arm(args):
     import numpy as np
@@ -647,6 +694,8 @@ def gpu_arm(args):
                                              for l in range(len(polys))],
                 "level_estimates_fp64": [[float(z.real), float(z.imag)] for z in m64],
                 "level_estimates_mixed": [[float(z.real), float(z.imag)] for z in m32]}
+        fp64["correction_levels"] = correction_levels(wl, polys, m64, v64, x64, m32, x32, t64, ms_per_step)
+        fp64["equal_se_speedup_with_corrections"] = fp64["correction_levels"].pop("equal_se_speedup")
 
     # ---------------------------------------------------------- the rest of the paper's estimate (Eq. (2))
     # Tr(A^{-1} - M_1), the first Monte Carlo of Sec. 5 step 3a: deflated PP-GMRES solves (FP64) on a

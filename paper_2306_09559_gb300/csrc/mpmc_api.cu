@@ -2166,11 +2166,15 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                 consider(per);
             }
             if (!rc && (user_sweep & 1) && fsweep_supported(h->storage, h->g, nb)) {
-                h->use_sweep = 1;
-                for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
-                    h->sweep_ts = ts;
-                    if (time_class(nb, 0, &per)) break;
-                    consider(per);
+                // t-sweep form, with links read from global memory and (bit 16) staged with the planes
+                for (int lsm : {0, 16}) {
+                    if (lsm && !(user_sweep & 16)) continue;
+                    h->use_sweep = 1 | lsm;
+                    for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
+                        h->sweep_ts = ts;
+                        if (time_class(nb, 0, &per)) break;
+                        consider(per);
+                    }
                 }
             }
         } else if (!rc && (user_sweep & 8) && sweep_supported(h->storage, h->g, nb)) {
@@ -2187,7 +2191,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     if (!rc && bnb == 0) rc = fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
     // phase 2: at that width, the undotted and outer classes choose among the site-parallel
     // kernel, the issue-lean kernel and its t-sweep form with the parameters found above
-    int fast_mask = bfast & 1, sweep_mask = bsweep & 9;
+    int fast_mask = bfast & 1, sweep_mask = bsweep & 25;
     if (!rc) {
         h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
         h->fast_sl = bfsl;
@@ -2201,7 +2205,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
             for (int c = 0; c < 3 && !rc; ++c) {
                 if ((c >= 1 && !can_fast) || (c == 2 && !can_sweep)) continue;
                 h->use_fast = c >= 1 ? bit : 0;
-                h->use_sweep = (c == 2 ? bit : 0) | (bsweep & 8);
+                h->use_sweep = (c == 2 ? bit | (bsweep & 16) : 0) | (bsweep & 8);
                 double per;
                 if (time_class(bnb, cls, &per)) break;
                 if (per < bper) { bper = per; bf = c >= 1; bs = c == 2; }

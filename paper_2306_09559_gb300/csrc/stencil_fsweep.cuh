@@ -221,22 +221,48 @@ __global__ void __launch_bounds__(LSM ? 128 : 8 * (NB < 32 ? NB : 32), LSM ? 3 :
             float2 up[6], lr[6], lj[6], p[12];
 #pragma unroll
             for (int i = 0; i < 6; ++i) up[i] = lr[i] = lj[i] = make_float2(0.f, 0.f);
-            if (bx == 0) srow(P0, sib + 1, p); else grow(tp + nxf, p);
-            fast::hop_p<0, true, LSM>(p, Lxf, 1.f, false, up, lr, lj);
-            if (bx == 1) srow(P0, sib - 1, p); else grow(tp + nxb, p);
-            fast::hop_p<0, false, LSM>(p, Lxb, 1.f, false, up, lr, lj);
-            if (by == 0) srow(P0, sib + 2, p); else grow(tp + nyf, p);
-            fast::hop_p<1, true, LSM>(p, Lyf, 1.f, false, up, lr, lj);
-            if (by == 1) srow(P0, sib - 2, p); else grow(tp + nyb, p);
-            fast::hop_p<1, false, LSM>(p, Lyb, 1.f, false, up, lr, lj);
-            if (bz == 0) srow(P0, sib + 4, p); else grow(tp + nzf, p);
-            fast::hop_p<2, true, LSM>(p, Lzf, 1.f, false, up, lr, lj);
-            if (bz == 1) srow(P0, sib - 4, p); else grow(tp + nzb, p);
-            fast::hop_p<2, false, LSM>(p, Lzb, 1.f, false, up, lr, lj);
-            srow(Pp, sib, p);
-            fast::hop_p<3, true, LSM>(p, Ltf, -1.f, af, up, lr, lj);
-            srow(Pm, sib, p);
-            fast::hop_p<3, false, LSM>(p, Ltb, -1.f, ab, up, lr, lj);
+            if constexpr (LSM) {
+                // the three out-of-block neighbour rows are the only global loads left: issue them
+                // all first and start with the two t-hops from shared memory, so that their L2
+                // latency overlaps arithmetic (the register budget of 3 CTAs per SM allows it)
+                float2 gx[12], gy[12], gz[12];
+                grow(tp + (bx ? nxf : nxb), gx);
+                grow(tp + (by ? nyf : nyb), gy);
+                grow(tp + (bz ? nzf : nzb), gz);
+                srow(Pp, sib, p);
+                fast::hop_p<3, true, LSM>(p, Ltf, -1.f, af, up, lr, lj);
+                srow(Pm, sib, p);
+                fast::hop_p<3, false, LSM>(p, Ltb, -1.f, ab, up, lr, lj);
+                if (bx == 0) srow(P0, sib + 1, p);
+                fast::hop_p<0, true, LSM>(bx == 0 ? p : gx, Lxf, 1.f, false, up, lr, lj);
+                if (bx == 1) srow(P0, sib - 1, p);
+                fast::hop_p<0, false, LSM>(bx == 1 ? p : gx, Lxb, 1.f, false, up, lr, lj);
+                if (by == 0) srow(P0, sib + 2, p);
+                fast::hop_p<1, true, LSM>(by == 0 ? p : gy, Lyf, 1.f, false, up, lr, lj);
+                if (by == 1) srow(P0, sib - 2, p);
+                fast::hop_p<1, false, LSM>(by == 1 ? p : gy, Lyb, 1.f, false, up, lr, lj);
+                if (bz == 0) srow(P0, sib + 4, p);
+                fast::hop_p<2, true, LSM>(bz == 0 ? p : gz, Lzf, 1.f, false, up, lr, lj);
+                if (bz == 1) srow(P0, sib - 4, p);
+                fast::hop_p<2, false, LSM>(bz == 1 ? p : gz, Lzb, 1.f, false, up, lr, lj);
+            } else {
+                if (bx == 0) srow(P0, sib + 1, p); else grow(tp + nxf, p);
+                fast::hop_p<0, true, LSM>(p, Lxf, 1.f, false, up, lr, lj);
+                if (bx == 1) srow(P0, sib - 1, p); else grow(tp + nxb, p);
+                fast::hop_p<0, false, LSM>(p, Lxb, 1.f, false, up, lr, lj);
+                if (by == 0) srow(P0, sib + 2, p); else grow(tp + nyf, p);
+                fast::hop_p<1, true, LSM>(p, Lyf, 1.f, false, up, lr, lj);
+                if (by == 1) srow(P0, sib - 2, p); else grow(tp + nyb, p);
+                fast::hop_p<1, false, LSM>(p, Lyb, 1.f, false, up, lr, lj);
+                if (bz == 0) srow(P0, sib + 4, p); else grow(tp + nzf, p);
+                fast::hop_p<2, true, LSM>(p, Lzf, 1.f, false, up, lr, lj);
+                if (bz == 1) srow(P0, sib - 4, p); else grow(tp + nzb, p);
+                fast::hop_p<2, false, LSM>(p, Lzb, 1.f, false, up, lr, lj);
+                srow(Pp, sib, p);
+                fast::hop_p<3, true, LSM>(p, Ltf, -1.f, af, up, lr, lj);
+                srow(Pm, sib, p);
+                fast::hop_p<3, false, LSM>(p, Ltb, -1.f, ab, up, lr, lj);
+            }
             srow(P0, sib, p);   // own row
 
             const size_t off = ((size_t)site * 12 * NB + col) * 2;
