@@ -496,6 +496,36 @@ def correction_levels(wl, polys, m64, v64, x64, mmix, xmix, t64, tmix):
     return out
 
 
+def kernel_sources_digest():
+    """Digest of the stencil kernel sources: a DRAM-traffic figure taken from an ncu capture
+    holds only while these are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_09559_gb300", "csrc")
+    for f in ("stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh", "tc.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel, storage, nb, V):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary profiles/dram_traffic.md
+    (a row per capture: kernel, storage, block width, lattice, bytes per launch, source digest),
+    scaled from the captured lattice to V sites (the traffic of the t-sweep grows with the
+    sites swept); None if no capture matches or the sources changed since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None, None
+    digest = kernel_sources_digest()
+    for line in open(path):
+        f = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(f) < 6 or f[0] != kernel or f[1] != storage or f[2] != str(nb) or f[5] != digest:
+            continue
+        dims = [int(x) for x in f[3].split("x")]
+        vcap = dims[0] * dims[1] * dims[2] * dims[3]
+        return float(f[4]) * V / vcap, f"ncu capture on {f[3]} (same kernel and block width), scaled by {V}/{vcap} sites"
+    return None, None
+
+
 # ------------------------------------------------------------------ GPU arm
 def gpu_arm(args):
     import numpy as np
@@ -754,12 +784,16 @@ def gpu_arm(args):
     alu = {"achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak,
            "flops_per_launch": flops_per_launch, "peak_source": "measured: mpmc_fma_peak(FP32)",
            "nominal_peak": 152 * 128 * 2 * sm_max * 1e6 / 1e12}
+    traffic, traffic_src = args.traffic, "--traffic" if args.traffic is not None else None
+    if traffic is None:
+        traffic, traffic_src = captured_traffic(dom, args.precision, block, wl.V)
     if args.precision != "fp64" and t_alu > t_hbm:
         # BF16-stored spinors: the FP32 arithmetic floor lies above the HBM floor
-        roofline = {"bound": "alu", **alu, "traffic": args.traffic, "hbm_frac": achieved_gbs / hbm}
+        roofline = {"bound": "alu", **alu, "traffic": traffic, "hbm_frac": achieved_gbs / hbm}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "traffic": args.traffic, "alu": alu}
+                    "frac": achieved_gbs / hbm, "traffic": traffic, "alu": alu}
+    roofline["traffic_source"] = traffic_src
     roofline.update({"kernel": kernel, "hbm_peak_source": src, "avg_launch_ms": avg_ms, "launches": dk["launches"],
                      "share_of_step": dk["ms"] / t_local if t_local else None,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "kernel_mix": kernel_mix,
