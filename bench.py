@@ -496,28 +496,41 @@ def correction_levels(wl, polys, m64, v64, x64, mmix, xmix, t64, tmix):
     return out
 
 
-def kernel_sources_digest():
-    """Digest of the stencil kernel sources: a DRAM-traffic figure taken from an ncu capture
-    holds only while these are unchanged."""
+# sources of each t-sweep form: a DRAM-traffic figure from an ncu capture holds while they are unchanged
+FORM_SOURCES = {
+    "k_fsweep": ("stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh", "tc.cuh"),
+    "k_fsweep_lsm": ("stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh", "tc.cuh"),
+    "k_fsweep_w": ("stencil_fsweep_w.cuh", "stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh",
+                   "tc.cuh"),
+}
+
+
+def fsweep_form(sweep_mask):
+    """Name of the t-sweep form a sweep option mask in effect runs (mpmc_get_option)."""
+    return "k_fsweep_w" if sweep_mask & 32 else "k_fsweep_lsm" if sweep_mask & 16 else "k_fsweep"
+
+
+def kernel_sources_digest(form="k_fsweep_lsm"):
+    """Digest of the sources of one t-sweep form (first 16 hex digits of a SHA-256)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_09559_gb300", "csrc")
-    for f in ("stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh", "tc.cuh"):
+    for f in FORM_SOURCES[form]:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def captured_traffic(kernel, storage, nb, V):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary profiles/dram_traffic.md
-    (a row per capture: kernel, storage, block width, lattice, bytes per launch, source digest),
-    scaled from the captured lattice to V sites (the traffic of the t-sweep grows with the
-    sites swept); None if no capture matches or the sources changed since."""
+    """DRAM bytes per launch of `kernel` (a t-sweep form) from the committed ncu summary
+    profiles/dram_traffic.md (a row per capture: kernel, storage, block width, lattice, bytes per
+    launch, source digest), scaled from the captured lattice to V sites (the traffic of the t-sweep
+    grows with the sites swept); None if no capture matches or the sources changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in FORM_SOURCES:
         return None, None
-    digest = kernel_sources_digest()
+    digest = kernel_sources_digest(kernel)
     for line in open(path):
-        f = [x.strip() for x in line.strip().strip("|").split("|")]
+        f = [x.strip().strip("`") for x in line.strip().strip("|").split("|")]
         if len(f) < 6 or f[0] != kernel or f[1] != storage or f[2] != str(nb) or f[5] != digest:
             continue
         dims = [int(x) for x in f[3].split("x")]
@@ -761,7 +774,11 @@ def gpu_arm(args):
 
     # ---------------------------------------------------------- roofline of the dominant kernel
     hbm, sm_max, src = peaks()
-    # the dominant kernel: the stencil kernel with the largest share of the timed steps
+    # the dominant kernel: the stencil kernel with the largest share of the timed steps (the t-sweep
+    # class named by the form the handle runs)
+    sweep_now = hm.mpmc_get_option(G.OPT_SWEEP_STENCIL)
+    if "k_fsweep" in per_kernel:
+        per_kernel[fsweep_form(sweep_now)] = per_kernel.pop("k_fsweep")
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dk = per_kernel[dom]
     avg_ms = dk["ms"] / dk["launches"]

@@ -120,16 +120,20 @@ void fast_geometry(const Geom& g, FastArgs& a);
 // t-sweep form of the issue-lean kernels (stencil_fsweep.cu): kinds 0, 1,
 // 3, 4; even lx, ly, lz; the input block read by TMA through a tensor map
 // made by fsweep_make_map; accumulator rows cfg.rows.
-// lsm: the variant that stages each plane's links in shared memory with the spinor rows
-// (tile width 16 right-hand sides; its own tensor maps and launch shapes)
+// var: 0 links read from global memory (tile width min(nb, 32)); 1 each plane's links staged in
+// shared memory with its spinor rows (tile width 16); 2 warp-per-site form with staged links (tile
+// width 32, nb >= 32; nb = 16 runs variant 1).  fsweep_variant maps the sweep option mask (bit 4:
+// staged links, bit 5: warp-per-site) and nb to var; fsweep_tile gives its tile width.
 bool fsweep_supported(int storage, const Geom& g, int nb);
-SweepCfg fsweep_config(const Geom& g, int nb, int ts, bool lsm);
+int fsweep_variant(int mask, int nb);
+int fsweep_tile(int var, int nb);
+SweepCfg fsweep_config(const Geom& g, int nb, int ts, int var);
 // Launch order of the (lx/2)(ly/2)(lz/2) site blocks along a Morton (Z-order) curve of the
 // block grid, so that CTAs running at the same time cover compact regions of the lattice
 void fsweep_morton_order(const Geom& g, int* order);
-bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, bool lsm);
+bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, int tw);
 int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepCfg& c, const void* map, int* err,
-                  cudaStream_t s, bool lsm);
+                  cudaStream_t s, int var);
 // Z4 words of a noise block: words[site][col] = Philox word 0 of (j0 + col, site, level)
 void launch_noise_words(const Geom& g, int nb, const NoiseSpec& ns, uint32_t* words, cudaStream_t s);
 // expanded links (re, re, im, im) in float from scale * complex-double [mu][site][3][3]

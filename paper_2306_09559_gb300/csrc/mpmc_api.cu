@@ -108,8 +108,9 @@ struct mpmc_ctx {
     // t-sweep stencil: option, t-segment length (0 automatic), tensor maps of input buffers
     // Stencil step classes: bit 0 dotted steps (single / projected chains, incl. the noise-started
     // first step), bit 1 undotted steps (inner steps of composite chains), bit 2 outer steps.
-    int use_sweep = 23;           // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep;
-                                  // bit 4: that form with each plane's links staged in shared memory
+    int use_sweep = 55;           // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep;
+                                  // bit 4: that form with each plane's links staged in shared memory;
+                                  // bit 5: its warp-per-site form (blocks of 32 or more columns)
     int sweep_ts = 0;
     int use_fast = 7;             // issue-lean kernels per class (FP32 / BF16S, block widths 16 .. 1024)
     int fast_sl = 1;              // sites per thread of the issue-lean kernels
@@ -229,7 +230,7 @@ int set_cfg(mpmc_ctx* h, Workspace& w) {
         w.fast_gx = (h->g.V + per - 1) / per;
     }
     w.fsweep = w.fast && (h->use_sweep & h->use_fast & 7) && fsweep_supported(w.storage, h->g, w.nb);
-    if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts, (h->use_sweep & 16) != 0);
+    if (w.fsweep) w.fsw = fsweep_config(h->g, w.nb, h->sweep_ts, fsweep_variant(h->use_sweep, w.nb));
     if (w.fsweep && !h->blk_order) {
         std::vector<int> order((size_t)w.fsw.nblk);
         fsweep_morton_order(h->g, order.data());
@@ -353,7 +354,7 @@ const void* sweep_map(mpmc_ctx* h, const Workspace& ws, const void* in, int kind
     for (const SweepMap& m : h->maps)
         if (m.p == in && m.storage == ws.storage && m.nb == ws.nb && m.V == h->g.V && m.kind == kind) return m.m;
     SweepMap m;
-    const bool made = kind ? fsweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb, kind == 2)
+    const bool made = kind ? fsweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb, kind == 2 ? 16 : std::min(ws.nb, 32))
                            : sweep_make_map(m.m, ws.storage, in, h->g.V, ws.nb);
     if (!made) return nullptr;
     m.p = in;
@@ -424,12 +425,12 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         f.dot_w[1] = a.dot_w[1];
         f.alpha[0] = (float)a.alpha[0];
         f.alpha[1] = (float)a.alpha[1];
-        const bool lsm = (h->use_sweep & 16) != 0;
-        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, lsm ? 2 : 1)
+        const int var = fsweep_variant(h->use_sweep, ws.nb);
+        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, var == 1 ? 2 : 1)
                                                                             : nullptr;
         prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
-            if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream, lsm))
+            if (launch_fsweep(ws.storage, ws.nb, kind, f, ws.fsw, fmap, h->d_err, h->stream, var))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep step launch failed");
         } else if (launch_fast(ws.storage, ws.nb, kind, f, ws.fast_gx, h->stream)) {
             return fail(h, MPMC_ECUDA, "issue-lean step launch failed");
@@ -479,11 +480,11 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
             f.beta[i] = (float)o.beta[i];
             f.gamma[i] = (float)o.gamma[i];
         }
-        const bool lsm = (h->use_sweep & 16) != 0;
-        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, lsm ? 2 : 1) : nullptr;
+        const int var = fsweep_variant(h->use_sweep, ws.nb);
+        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, var == 1 ? 2 : 1) : nullptr;
         prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
-            if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream, lsm))
+            if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream, var))
                 return fail(h, MPMC_ECUDA, "issue-lean t-sweep outer launch failed");
         } else if (launch_fast(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fast_gx, h->stream)) {
             return fail(h, MPMC_ECUDA, "issue-lean outer launch failed");
@@ -2165,10 +2166,12 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                 consider(per);
             }
             if (!rc && (user_sweep & 1) && fsweep_supported(h->storage, h->g, nb)) {
-                // t-sweep form, with links read from global memory and (bit 16) staged with the planes
-                for (int lsm : {0, 16}) {
-                    if (lsm && !(user_sweep & 16)) continue;
-                    h->use_sweep = 1 | lsm;
+                // t-sweep form, with links read from global memory, (bit 16) staged with the planes
+                // and (bit 32) staged, one warp per site
+                for (int v : {0, 16, 32}) {
+                    if (v && !(user_sweep & v)) continue;
+                    if (v == 32 && fsweep_variant(32, nb) != 2) continue;
+                    h->use_sweep = 1 | v;
                     for (int ts = h->g.lt; ts >= 2 && !rc; ts = (ts % 2 == 0 ? ts / 2 : 1)) {
                         h->sweep_ts = ts;
                         if (time_class(nb, 0, &per)) break;
@@ -2190,7 +2193,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     if (!rc && bnb == 0) rc = fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
     // phase 2: at that width, the undotted and outer classes choose among the site-parallel
     // kernel, the issue-lean kernel and its t-sweep form with the parameters found above
-    int fast_mask = bfast & 1, sweep_mask = bsweep & 25;
+    int fast_mask = bfast & 1, sweep_mask = bsweep & 57;
     if (!rc) {
         h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
         h->fast_sl = bfsl;
@@ -2204,7 +2207,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
             for (int c = 0; c < 3 && !rc; ++c) {
                 if ((c >= 1 && !can_fast) || (c == 2 && !can_sweep)) continue;
                 h->use_fast = c >= 1 ? bit : 0;
-                h->use_sweep = (c == 2 ? bit | (bsweep & 16) : 0) | (bsweep & 8);
+                h->use_sweep = (c == 2 ? bit | (bsweep & 48) : 0) | (bsweep & 8);
                 double per;
                 if (time_class(bnb, cls, &per)) break;
                 if (per < bper) { bper = per; bf = c >= 1; bs = c == 2; }
@@ -2241,13 +2244,14 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         const int shapes[][3] = {{bR, bbx, bsl}, {1, 32, 2}, {1, 64, 1}, {2, 32, 1}};
         for (const auto& sh : shapes)
             for (int fm : {0, 1, 3, 5, 7})
-                for (int sm : {0, 7, 23}) {
+                for (int sm : {0, 7, 23, 39}) {
                     if (sm && !fsw) continue;
                     if (fm == 7 && sh != shapes[0]) continue;   // no site-parallel step left to shape
-                    // the links-staged t-sweep (bit 16) only with the shape found in phase 1
-                    if (sm == 23 && (sh != shapes[0] || !(user_sweep & 16) || !(fm & 7))) continue;
+                    // the links-staged t-sweep forms (bits 16, 32) only with the shape found in phase 1
+                    if (sm > 7 && (sh != shapes[0] || !(user_sweep & sm & 48) || !(fm & 7))) continue;
+                    if (sm == 39 && fsweep_variant(32, bnb) != 2) continue;
                     const int f = fm & user_fast;
-                    const int sw = (sm & f & user_sweep) | (sm & user_sweep & 16) | (bsweep & 8);
+                    const int sw = (sm & f & user_sweep) | (sm & user_sweep & 48) | (bsweep & 8);
                     cand.push_back({f, sw, sh[0], sh[1], sh[2]});
                 }
         double tbest = INFINITY;
@@ -2294,7 +2298,7 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->use_tc = value != 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            if (value < 0 || value > 31) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 31");
+            if (value < 0 || value > 63) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 63");
             h->use_sweep = value;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
@@ -2341,13 +2345,16 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
             if (fast_supported(h->storage, cur_nb(h)) && fsweep_supported(h->storage, h->g, cur_nb(h)))
                 v |= h->use_sweep & h->use_fast & 7;
             if (sweep_supported(h->storage, h->g, cur_nb(h))) v |= h->use_sweep & 8;
-            if (v & 7) v |= h->use_sweep & 16;
+            if (v & 7) {
+                const int var = fsweep_variant(h->use_sweep, cur_nb(h));
+                v |= var == 2 ? 32 : var == 1 ? 16 : 0;
+            }
             *value = v;
             return MPMC_OK;
         }
         case MPMC_OPT_SWEEP_SEGMENT:
             *value = ((h->use_fast & 7) && fsweep_supported(h->storage, h->g, cur_nb(h)))
-                         ? fsweep_config(h->g, cur_nb(h), h->sweep_ts, (h->use_sweep & 16) != 0).ts
+                         ? fsweep_config(h->g, cur_nb(h), h->sweep_ts, fsweep_variant(h->use_sweep, cur_nb(h))).ts
                          : sweep_config(h->g, cur_nb(h), h->sweep_ts).ts;
             return MPMC_OK;
         case MPMC_OPT_FAST_STENCIL:

@@ -1,6 +1,7 @@
-// Instantiations and host side of the t-sweep issue-lean stencil kernels
-// (stencil_fsweep.cuh).
-#include "stencil_fsweep.cuh"
+// Host side of the t-sweep issue-lean stencil kernels (stencil_fsweep.cuh); their
+// instantiations are split over stencil_fsweep_{f32,bf16,w_f32,w_bf16}.cu so that they compile
+// in parallel.
+#include "stencil_fsweep_w.cuh"
 
 #include <algorithm>
 #include <utility>
@@ -8,59 +9,24 @@
 
 namespace mpmc {
 
-namespace {
-
-template <class S, int NB, int KIND, bool LSM>
-int launch_one(const CUtensorMap& map, const fsw::Geom4& g, int gx, int* err, cudaStream_t s) {
-    constexpr int TW = fsw::tile_width<NB, LSM>();
-    auto kern = fsw::k_fsweep<S, NB, KIND, LSM>;
-    constexpr int smem = fsw::smem_bytes<S, TW, LSM>();
-    static bool attr = false;   // one flag per instantiation
-    if (!attr) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
-        attr = true;
-    }
-    kern<<<dim3(gx * (NB / TW)), 8 * TW, smem, s>>>(map, g, err);
-    return cudaGetLastError() == cudaSuccess ? 0 : 1;
-}
-
-template <class S, int NB, bool LSM>
-int launch_nb(int kind, const CUtensorMap& m, const fsw::Geom4& g, int gx, int* err, cudaStream_t s) {
-    switch (kind) {
-        case 0: return launch_one<S, NB, 0, LSM>(m, g, gx, err, s);
-        case 1: return launch_one<S, NB, 1, LSM>(m, g, gx, err, s);
-        case 3: return launch_one<S, NB, 3, LSM>(m, g, gx, err, s);
-        case 4: return launch_one<S, NB, 4, LSM>(m, g, gx, err, s);
-        default: return 1;
-    }
-}
-
-template <class S, bool LSM>
-int launch_s(int nb, int kind, const CUtensorMap& m, const fsw::Geom4& g, int gx, int* err, cudaStream_t s) {
-    switch (nb) {
-        case 16: return launch_nb<S, 16, LSM>(kind, m, g, gx, err, s);
-        case 32: return launch_nb<S, 32, LSM>(kind, m, g, gx, err, s);
-        case 64: return launch_nb<S, 64, LSM>(kind, m, g, gx, err, s);
-        case 128: return launch_nb<S, 128, LSM>(kind, m, g, gx, err, s);
-        case 256: return launch_nb<S, 256, LSM>(kind, m, g, gx, err, s);
-        case 512: return launch_nb<S, 512, LSM>(kind, m, g, gx, err, s);
-        case 1024: return launch_nb<S, 1024, LSM>(kind, m, g, gx, err, s);
-        default: return 1;
-    }
-}
-
-}  // namespace
 
 bool fsweep_supported(int storage, const Geom& g, int nb) {
     return fast_supported(storage, nb) && g.lx % 2 == 0 && g.ly % 2 == 0 && g.lz % 2 == 0 && g.lt >= 2;
 }
 
-SweepCfg fsweep_config(const Geom& g, int nb, int ts, bool lsm) {
+int fsweep_variant(int mask, int nb) {
+    if (mask & 32) return nb >= 32 ? 2 : 1;
+    return (mask & 16) ? 1 : 0;
+}
+
+int fsweep_tile(int var, int nb) { return var == 2 ? fsw::WTW : var == 1 ? 16 : (nb < 32 ? nb : 32); }
+
+SweepCfg fsweep_config(const Geom& g, int nb, int ts, int var) {
     SweepCfg c;
-    const int tw = lsm ? 16 : (nb < 32 ? nb : 32);
+    const int tw = fsweep_tile(var, nb);
     c.nblk = (g.lx / 2) * (g.ly / 2) * (g.lz / 2);
     c.tiles = nb / tw;
-    const int per_sm = lsm ? 3 : 512 / (8 * tw);   // resident CTAs per SM
+    const int per_sm = var == 2 ? 2 : var == 1 ? 3 : 512 / (8 * tw);   // resident CTAs per SM
     if (ts <= 0) {
         // the longest segment that still fills two waves of the 152 SMs
         ts = g.lt;
@@ -87,10 +53,9 @@ void fsweep_morton_order(const Geom& g, int* order) {
 }
 
 // Rows of nb complex values (inner dimension 2 nb scalars, V*12 rows), TW-complex x 12-row boxes.
-bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, bool lsm) {
+bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, int tw) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
-    const int tw = lsm ? 16 : (nb < 32 ? nb : 32);
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || tw <= 0 || nb % tw) return false;
     const size_t es = storage == ST_F32 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)2 * nb, (cuuint64_t)V * 12};
     cuuint64_t strides[1] = {(cuuint64_t)2 * nb * es};
@@ -104,9 +69,10 @@ bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, bo
 }
 
 int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepCfg& c, const void* map, int* err,
-                  cudaStream_t s, bool lsm) {
-    if (!fast_supported(storage, nb)) return 1;
-    if (c.tiles != nb / (lsm ? 16 : (nb < 32 ? nb : 32))) return 1;   // shape made for the other variant
+                  cudaStream_t s, int var) {
+    if (!fast_supported(storage, nb) || var < 0 || var > 2) return 1;
+    if (var == 2 && nb < 32) var = 1;
+    if (c.tiles != nb / fsweep_tile(var, nb)) return 1;   // shape made for another variant
     fsw::Geom4 g;
     g.a = a;
     g.nblk = c.nblk;
@@ -114,10 +80,10 @@ int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepC
     g.nseg = c.nseg;
     const CUtensorMap& m = *reinterpret_cast<const CUtensorMap*>(map);
     if (storage == ST_F32)
-        return lsm ? launch_s<float, true>(nb, kind, m, g, c.rows, err, s)
-                   : launch_s<float, false>(nb, kind, m, g, c.rows, err, s);
-    return lsm ? launch_s<__nv_bfloat16, true>(nb, kind, m, g, c.rows, err, s)
-               : launch_s<__nv_bfloat16, false>(nb, kind, m, g, c.rows, err, s);
+        return var == 2 ? fsw::launch_w_f32(nb, kind, m, g, c.rows, err, s)
+                        : fsw::launch_f32(var, nb, kind, m, g, c.rows, err, s);
+    return var == 2 ? fsw::launch_w_bf16(nb, kind, m, g, c.rows, err, s)
+                    : fsw::launch_bf16(var, nb, kind, m, g, c.rows, err, s);
 }
 
 }  // namespace mpmc

@@ -1,0 +1,12 @@
+// FP32 instantiations of the warp-per-site t-sweep kernel k_fsweep_w.
+#include "stencil_fsweep_w.cuh"
+
+namespace mpmc {
+namespace fsw {
+
+int launch_w_f32(int nb, int kind, const CUtensorMap& m, const Geom4& g, int gx, int* err, cudaStream_t s) {
+    return launch_s<float, 2>(nb, kind, m, g, gx, err, s);
+}
+
+}  // namespace fsw
+}  // namespace mpmc

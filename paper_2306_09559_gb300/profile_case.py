@@ -29,7 +29,8 @@ def main(argv=None):
     ap.add_argument("--nb", type=int, default=32, help="noise columns per launch")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16s", "fp64"])
     ap.add_argument("--fast", type=int, default=7, help="MPMC_OPT_FAST_STENCIL step-class mask")
-    ap.add_argument("--sweep", type=int, default=23, help="MPMC_OPT_SWEEP_STENCIL mask (bit 16: links staged)")
+    ap.add_argument("--sweep", type=int, default=55,
+                    help="MPMC_OPT_SWEEP_STENCIL mask (bit 16: links staged, bit 32: warp-per-site form)")
     ap.add_argument("--segment", type=int, default=0, help="MPMC_OPT_SWEEP_SEGMENT (0: whole t extent)")
     ap.add_argument("--order", type=int, default=1, help="MPMC_OPT_SWEEP_ORDER")
     ap.add_argument("--launch", type=int, nargs=2, default=[1, 64], metavar=("R", "BX"))

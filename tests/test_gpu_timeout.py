@@ -26,10 +26,10 @@ def _built():
     G.lib()
 
 
-def _handle(prec, Z, lam, pair, polys):
+def _handle(prec, Z, lam, pair, polys, block=16):
     from test_gpu_parity import set_polys
     h = G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, prec, 1)
-    h.mpmc_set_block(16)
+    h.mpmc_set_block(block)
     h.mpmc_set_option(G.OPT_FAST_STENCIL, 7)
     h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 7)
     h.mpmc_set_option(G.OPT_SWEEP_SEGMENT, 4)           # planes 0 .. 5 in each CTA's ring
@@ -39,13 +39,15 @@ def _handle(prec, Z, lam, pair, polys):
 
 
 @pytest.mark.parametrize("skip", [1, 2, 5])
-@pytest.mark.parametrize("sweep", [7, 23])
+@pytest.mark.parametrize("sweep", [7, 23, 39])
 def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(skip, sweep):
+    """Every t-sweep form (links from global memory, staged, warp-per-site with blocks of 32)."""
     from test_gpu_parity import small_setup
     op, polys, lam, Z, pair = small_setup()
     polys = fp32_polys(polys)
     N = 24
-    with _handle(G.FP32, Z, lam, pair, polys) as h, _handle(G.FP32, Z, lam, pair, polys) as fresh:
+    block = 32 if sweep & 32 else 16
+    with _handle(G.FP32, Z, lam, pair, polys, block) as h, _handle(G.FP32, Z, lam, pair, polys, block) as fresh:
         for hh in (h, fresh):
             hh.mpmc_set_option(G.OPT_SWEEP_STENCIL, sweep)
         assert h.mpmc_get_option(G.OPT_SWEEP_STENCIL) == sweep
