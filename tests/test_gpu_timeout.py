@@ -45,8 +45,8 @@ def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(skip, swe
     from test_gpu_parity import small_setup
     op, polys, lam, Z, pair = small_setup()
     polys = fp32_polys(polys)
-    N = 24
     block = 32 if sweep & 32 else 16
+    N = block + block // 2            # two blocks of `block` columns, the second one ragged
     with _handle(G.FP32, Z, lam, pair, polys, block) as h, _handle(G.FP32, Z, lam, pair, polys, block) as fresh:
         for hh in (h, fresh):
             hh.mpmc_set_option(G.OPT_SWEEP_STENCIL, sweep)
