@@ -14,8 +14,9 @@ namespace fsw {
 // slots (spinor rows + the plane's links), two CTAs (16 warps) per SM at 128 registers.
 // No CTA-wide barrier per plane: each warp counts itself out of the slot it no longer needs and
 // the last of the eight issues the next plane's copies into it, so warps drift by up to a plane.
-// Hop order: the three out-of-block rows are loaded one hop ahead of use (global memory, L2),
-// the forward t-hop, whose plane is the one most recently issued, comes last.
+// Hop order: the out-of-block rows come from global memory (L2) ahead of use: x during the
+// previous plane, y before the backward t-hop, z before the y hops; the forward t-hop, whose
+// plane is the one most recently issued, comes last.
 constexpr int WRING = 3;
 constexpr int WTW = 32;
 template <class S> __host__ __device__ constexpr int wslot_bytes() { return plane_bytes<S, WTW>() + LINK_SLOT; }
@@ -190,6 +191,8 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
         for (int e = 0; e < 12; ++e) p[e] = Row<S>::ld(q + (size_t)e * NB * 2);
     };
 
+    float2 G[12];                              // out-of-block rows, one plane ahead for x
+    grow(t0 * plane + ox, G);
     bool ok = tc::mbar_wait(&full[0], 0, deadline) && tc::mbar_wait(&full[1], 0, deadline);
     if (!ok) s_fail = 1;
     for (int t = t0; t < t1; ++t) {
@@ -218,21 +221,25 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
             const float4* Ltf = Lc + (sib * 4 + 3) * 9;
             const float4* Ltb = Lm + (sib * 4 + 3) * 9;
 
-            float2 acc[12], G[12], H[12];
+            float2 acc[12], H[12];
 #pragma unroll
             for (int e = 0; e < 12; ++e) acc[e] = make_float2(0.f, 0.f);
             auto reg = [](const float2 (&r)[12]) { return [&r](int e) { return r[e]; }; };
-            grow(tp + ox, G);
-            hop_w<3, false>(srow(M, sib), Ltb, -1.f, ab, acc);
+            // G holds this plane's out-of-block x row (loaded during the previous plane)
             grow(tp + oy, H);
+            hop_w<3, false>(srow(M, sib), Ltb, -1.f, ab, acc);
             // x: out-of-block row (registers) and the in-block partner (shared memory); warp-uniform
             if (bx) { hop_w<0, true>(reg(G), Lxf, 1.f, false, acc); hop_w<0, false>(srow(C, sib - 1), Lxb, 1.f, false, acc); }
             else    { hop_w<0, false>(reg(G), Lxb, 1.f, false, acc); hop_w<0, true>(srow(C, sib + 1), Lxf, 1.f, false, acc); }
             grow(tp + oz, G);
             if (by) { hop_w<1, true>(reg(H), Lyf, 1.f, false, acc); hop_w<1, false>(srow(C, sib - 2), Lyb, 1.f, false, acc); }
             else    { hop_w<1, false>(reg(H), Lyb, 1.f, false, acc); hop_w<1, true>(srow(C, sib + 2), Lyf, 1.f, false, acc); }
-            if (bz) { hop_w<2, true>(reg(G), Lzf, 1.f, false, acc); hop_w<2, false>(srow(C, sib - 4), Lzb, 1.f, false, acc); }
-            else    { hop_w<2, false>(reg(G), Lzb, 1.f, false, acc); hop_w<2, true>(srow(C, sib + 4), Lzf, 1.f, false, acc); }
+            // z, then the next plane's x row into G, ahead of the in-block z hop, the t-hop and the stores
+            if (bz) hop_w<2, true>(reg(G), Lzf, 1.f, false, acc);
+            else    hop_w<2, false>(reg(G), Lzb, 1.f, false, acc);
+            if (t + 1 < t1) grow(tp + plane + ox, G);
+            if (bz) hop_w<2, false>(srow(C, sib - 4), Lzb, 1.f, false, acc);
+            else    hop_w<2, true>(srow(C, sib + 4), Lzf, 1.f, false, acc);
             ok = tc::mbar_wait(&full[(rel + 1) % WRING], (uint32_t)(((rel + 1) / WRING) & 1), deadline);
             if (!ok) {
                 s_fail = 1;
