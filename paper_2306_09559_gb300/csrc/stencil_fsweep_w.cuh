@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
         const float4* Ue = a.Ue;
         const int xm = X0 > 0 ? X0 - 1 : a.lx - 1, ym = Y0 > 0 ? Y0 - 1 : a.ly - 1;
         const int zm = Z0 > 0 ? Z0 - 1 : a.lz - 1;
+        const int xp = X0 + 2 < a.lx ? X0 + 2 : 0, yp = Y0 + 2 < a.ly ? Y0 + 2 : 0;
+        const int zp = Z0 + 2 < a.lz ? Z0 + 2 : 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int u = q & 1, v = q >> 1;
@@ -163,6 +165,15 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
             tc::bulk_load(L + LINK_YB + q * 9, Ue + ((size_t)sy2 * 4 + 1) * 9, 9 * 16, bar);
             const int sz2 = t * plane + (zm * a.ly + (Y0 + v)) * a.lx + (X0 + u);
             tc::bulk_load(L + LINK_ZB + q * 9, Ue + ((size_t)sz2 * 4 + 2) * 9, 9 * 16, bar);
+            // the plane's out-of-block neighbour rows into L2 (the warps read them one or two planes
+            // later with plain loads): the x, y, z faces on both sides, 4 rows each
+            const int col0 = tile * TW * 2;
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + ((Z0 + v) * a.ly + (Y0 + u)) * a.lx + xm));
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + ((Z0 + v) * a.ly + (Y0 + u)) * a.lx + xp));
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + ((Z0 + v) * a.ly + ym) * a.lx + (X0 + u)));
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + ((Z0 + v) * a.ly + yp) * a.lx + (X0 + u)));
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + (zm * a.ly + (Y0 + v)) * a.lx + (X0 + u)));
+            tc::tma_prefetch_2d(&tin, col0, 12 * (t * plane + (zp * a.ly + (Y0 + v)) * a.lx + (X0 + u)));
         }
     };
     if (tid == 0) {
