@@ -10,26 +10,17 @@ namespace fsw {
 // ---------------------------------------------------------------------------------------------
 // Warp-per-site form (k_fsweep_w): TW = 32 right-hand sides, 256 threads, warp w owns site w of
 // the 2 x 2 x 2 block, so which of a site's x / y / z neighbours lie outside the block is the
-// same for all lanes of a warp and the hops need no per-lane selects.  Two CTAs (16 warps) per SM
-// at 128 registers.  Shared memory: a ring of four plane slots (the block's spinor rows and t-links
-// of a plane, filled by TMA / bulk copies) and a ring of two slots for the x / y / z links a plane's
-// hops use, so that each plane is issued well over a plane ahead of its use.  No CTA-wide barrier
-// per plane: each warp counts itself out of the slots it no longer needs and the last of the eight
-// (all its lanes) issues the copies that refill them, so warps drift by up to two planes.
+// same for all lanes of a warp and the hops need no per-lane selects.  Ring of three plane
+// slots (spinor rows + the plane's links), two CTAs (16 warps) per SM at 128 registers.
+// No CTA-wide barrier per plane: each warp counts itself out of the slot it no longer needs and
+// the last of the eight issues the next plane's copies into it, so warps drift by up to a plane.
 // Hop order: the out-of-block rows come from global memory (L2) ahead of use: x during the
 // previous plane, y before the backward t-hop, z before the y hops; the forward t-hop, whose
-// plane is the one most recently needed, comes last.
-constexpr int WRING = 4;                                  // spinor-plane slots
-constexpr int WLRING = 2;                                 // x / y / z link slots
+// plane is the one most recently issued, comes last.
+constexpr int WRING = 3;
 constexpr int WTW = 32;
-constexpr int WT_LINKS = 8 * 9;                           // float4: the block's t-links of a plane
-constexpr int WL_OWN = 0, WL_XB = 8 * 27, WL_YB = WL_XB + 36, WL_ZB = WL_YB + 36;   // float4 offsets
-constexpr int WL_BYTES = (WL_ZB + 36) * 16;               // 5184: own x, y, z links [w][mu][9], backward
-constexpr int WL_SLOT = (WL_BYTES + 127) / 128 * 128;     // 5248
-template <class S> __host__ __device__ constexpr int wslot_bytes() { return plane_bytes<S, WTW>() + WT_LINKS * 16; }
-template <class S> __host__ __device__ constexpr int wsmem_bytes() {
-    return WRING * wslot_bytes<S>() + WLRING * WL_SLOT + (WRING + WLRING) * 8 + 128;
-}
+template <class S> __host__ __device__ constexpr int wslot_bytes() { return plane_bytes<S, WTW>() + LINK_SLOT; }
+template <class S> __host__ __device__ constexpr int wsmem_bytes() { return WRING * wslot_bytes<S>() + WRING * 8 + 128; }
 
 // One hop onto the 12 accumulators acc (spins 0-1 then 2-3, three colours each), the row given
 // component by component by src(e) (a register array or shared-memory loads made where used).
@@ -107,16 +98,12 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
     constexpr int RS = RB / (int)sizeof(S);
     constexpr bool OUTER = KIND >= 3;
     constexpr bool DOT = KIND == 1 || KIND == 4;
-    static_assert(SB % 128 == 0 && PB % 128 == 0, "slots on 128-byte boundaries");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
-    uint8_t* lring = smem + WRING * SB;
-    uint64_t* full = reinterpret_cast<uint64_t*>(lring + WLRING * WL_SLOT);   // spinor slots
-    uint64_t* lfull = full + WRING;                                             // link slots
-    __shared__ int s_out[WRING];      // warps counted out after each plane (monotone; 8 per plane)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + WRING * SB);
+    __shared__ int s_out[WRING];      // warps counted out of each slot (monotone; 8 per use)
     __shared__ volatile int s_fail;
-    __shared__ volatile int s_issued;   // highest spinor plane whose copies were issued
-    __shared__ volatile int s_lissued;  // highest link plane whose copies were issued
+    __shared__ volatile int s_issued; // highest plane index whose copies were issued
     __shared__ float4 ctab[4];
     double2 (*red)[TW] = reinterpret_cast<double2 (*)[TW]>(smem);   // dot reduction, over slot 0 at the end
 
@@ -148,71 +135,49 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
     const int t0 = seg * g.ts;
     const int t1 = min(t0 + g.ts, a.lt);
     const int nrel = t1 - t0 + 2;              // planes t0-1 .. t1, rel = q - (t0 - 1)
-    const float4* Ue = a.Ue;
-    // block site w at plane t (lattice index)
-    auto bsite = [&](int t, int w) {
-        return t * plane + ((Z0 + (w >> 2)) * a.ly + (Y0 + ((w >> 1) & 1))) * a.lx + (X0 + (w & 1));
-    };
 
-    // Copies of spinor plane `rel` (rows + t-links, spinor slot rel % WRING) and of the x / y / z links
-    // of plane `lrel` (link slot (lrel - 1) % WLRING; -1: none), by the 32 lanes of one warp.
-    auto issue = [&](int rel, int lrel) {
-        const bool pl = rel >= 0 && rel + 1 != a.skip_copy;   // test hook (1-based; 0 = off): left out
-        if (lane == 0) {
-            if (rel >= 0) s_issued = rel;
-            if (lrel >= 0) s_lissued = lrel;
-            if (pl) tc::mbar_expect_tx(&full[rel % WRING], (uint32_t)(PB + WT_LINKS * 16));
-            if (lrel >= 0) tc::mbar_expect_tx(&lfull[(lrel - 1) % WLRING], (uint32_t)WL_BYTES);
+    auto issue = [&](int rel) {                // one thread
+        s_issued = rel;
+        if (rel + 1 == a.skip_copy) return;    // test hook (1-based; 0 = off): this copy is never issued
+        const int t = (t0 - 1 + rel + a.lt) % a.lt;
+        uint64_t* bar = &full[rel % WRING];
+        uint8_t* dst = smem + (rel % WRING) * SB;
+        tc::mbar_expect_tx(bar, (uint32_t)(PB + LINK_BYTES));
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int s = t * plane + ((Z0 + (w >> 2)) * a.ly + (Y0 + ((w >> 1) & 1))) * a.lx + (X0 + (w & 1));
+            tc::tma_load_2d(dst + w * RB, &tin, tile * TW * 2, s * 12, bar);
         }
-        __syncwarp();
-        if (pl) {
-            const int t = (t0 - 1 + rel + a.lt) % a.lt;
-            uint8_t* dst = smem + (rel % WRING) * SB;
-            uint64_t* bar = &full[rel % WRING];
-            if (lane < 8) {
-                tc::tma_load_2d(dst + lane * RB, &tin, tile * TW * 2, bsite(t, lane) * 12, bar);
-            } else if (lane < 16) {
-                const int w = lane - 8;
-                tc::bulk_load(reinterpret_cast<float4*>(dst + PB) + w * 9, Ue + ((size_t)bsite(t, w) * 4 + 3) * 9,
-                              9 * 16, bar);
-            }
-        }
-        if (lrel >= 0) {
-            const int t = t0 - 1 + lrel;       // a link plane is one of t0 .. t1 - 1
-            float4* L = reinterpret_cast<float4*>(lring + ((lrel - 1) % WLRING) * WL_SLOT);
-            uint64_t* bar = &lfull[(lrel - 1) % WLRING];
-            if (lane >= 16 && lane < 24) {
-                const int w = lane - 16;
-                tc::bulk_load(L + WL_OWN + w * 27, Ue + (size_t)bsite(t, w) * 36, 27 * 16, bar);
-            } else if (lane >= 24 || lane < 4) {
-                // backward links of the hops that leave the block: q = (u, v) over the face
-                const int k = lane >= 24 ? lane - 24 : lane + 8;    // 0 .. 11
-                const int dir = k >> 2, q = k & 3, u = q & 1, v = q >> 1;
-                const int xm = X0 > 0 ? X0 - 1 : a.lx - 1, ym = Y0 > 0 ? Y0 - 1 : a.ly - 1;
-                const int zm = Z0 > 0 ? Z0 - 1 : a.lz - 1;
-                int sb;
-                if (dir == 0) sb = t * plane + ((Z0 + v) * a.ly + (Y0 + u)) * a.lx + xm;        // (by, bz) = (u, v)
-                else if (dir == 1) sb = t * plane + ((Z0 + v) * a.ly + ym) * a.lx + (X0 + u);   // (bx, bz) = (u, v)
-                else sb = t * plane + (zm * a.ly + (Y0 + v)) * a.lx + (X0 + u);                 // (bx, by) = (u, v)
-                tc::bulk_load(L + WL_XB + dir * 36 + q * 9, Ue + ((size_t)sb * 4 + dir) * 9, 9 * 16, bar);
-            }
+        float4* L = reinterpret_cast<float4*>(dst + PB);
+        const float4* Ue = a.Ue;
+        const int xm = X0 > 0 ? X0 - 1 : a.lx - 1, ym = Y0 > 0 ? Y0 - 1 : a.ly - 1;
+        const int zm = Z0 > 0 ? Z0 - 1 : a.lz - 1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = q & 1, v = q >> 1;
+            const int s0 = t * plane + ((Z0 + v) * a.ly + (Y0 + u)) * a.lx + X0;
+            tc::bulk_load(L + 2 * q * 36, Ue + (size_t)s0 * 36, 2 * 36 * 16, bar);
+            const int sx = t * plane + ((Z0 + v) * a.ly + (Y0 + u)) * a.lx + xm;
+            tc::bulk_load(L + LINK_XB + q * 9, Ue + ((size_t)sx * 4 + 0) * 9, 9 * 16, bar);
+            const int sy2 = t * plane + ((Z0 + v) * a.ly + ym) * a.lx + (X0 + u);
+            tc::bulk_load(L + LINK_YB + q * 9, Ue + ((size_t)sy2 * 4 + 1) * 9, 9 * 16, bar);
+            const int sz2 = t * plane + (zm * a.ly + (Y0 + v)) * a.lx + (X0 + u);
+            tc::bulk_load(L + LINK_ZB + q * 9, Ue + ((size_t)sz2 * 4 + 2) * 9, 9 * 16, bar);
         }
     };
     if (tid == 0) {
         s_fail = 0;
         s_issued = -1;
-        s_lissued = -1;
         for (int b = 0; b < WRING; ++b) {
             tc::mbar_init(&full[b], 1);
             s_out[b] = 0;
         }
-        for (int b = 0; b < WLRING; ++b) tc::mbar_init(&lfull[b], 1);
         tc::fence_mbar_init();
     }
     if (tid < 4) ctab[tid] = fast::z4_conj_entry(tid);
     __syncthreads();
-    if (sib == 0)
-        for (int rel = 0; rel < WRING && rel < nrel; ++rel) issue(rel, rel >= 1 && rel <= WLRING && rel <= nrel - 2 ? rel : -1);
+    if (tid == 0)
+        for (int rel = 0; rel < WRING && rel < nrel; ++rel) issue(rel);
 
     const float2 al = make_float2(a.alpha[0], a.alpha[1]);
     const float2 mk = make_float2(-a.kappa, -a.kappa);
@@ -234,10 +199,6 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
         const int rel = t - t0 + 1;
         if (ok && s_fail) ok = false;          // another warp gave up: no new plane is coming
         if (ok) {
-            ok = tc::mbar_wait(&lfull[(rel - 1) % WLRING], (uint32_t)(((rel - 1) / WLRING) & 1), deadline);
-            if (!ok) s_fail = 1;
-        }
-        if (ok) {
             const uint8_t* C = smem + (rel % WRING) * SB;
             const uint8_t* M = smem + ((rel - 1) % WRING) * SB;
             const uint8_t* N = smem + ((rel + 1) % WRING) * SB;
@@ -249,15 +210,16 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
             const int tp = t * plane;
             const int site = tp + sxyz;
             const bool af = a.bc_t < 0 && t + 1 == a.lt, ab = a.bc_t < 0 && t == 0;
-            const float4* Lc = reinterpret_cast<const float4*>(lring + ((rel - 1) % WLRING) * WL_SLOT);
-            const float4* Lxf = Lc + WL_OWN + (sib * 3 + 0) * 9;
-            const float4* Lxb = bx ? Lc + WL_OWN + ((sib - 1) * 3 + 0) * 9 : Lc + WL_XB + (by + 2 * bz) * 9;
-            const float4* Lyf = Lc + WL_OWN + (sib * 3 + 1) * 9;
-            const float4* Lyb = by ? Lc + WL_OWN + ((sib - 2) * 3 + 1) * 9 : Lc + WL_YB + (bx + 2 * bz) * 9;
-            const float4* Lzf = Lc + WL_OWN + (sib * 3 + 2) * 9;
-            const float4* Lzb = bz ? Lc + WL_OWN + ((sib - 4) * 3 + 2) * 9 : Lc + WL_ZB + (bx + 2 * by) * 9;
-            const float4* Ltf = reinterpret_cast<const float4*>(C + PB) + sib * 9;
-            const float4* Ltb = reinterpret_cast<const float4*>(M + PB) + sib * 9;
+            const float4* Lc = reinterpret_cast<const float4*>(C + PB);
+            const float4* Lm = reinterpret_cast<const float4*>(M + PB);
+            const float4* Lxf = Lc + (sib * 4 + 0) * 9;
+            const float4* Lxb = bx ? Lc + ((sib - 1) * 4 + 0) * 9 : Lc + LINK_XB + (by + 2 * bz) * 9;
+            const float4* Lyf = Lc + (sib * 4 + 1) * 9;
+            const float4* Lyb = by ? Lc + ((sib - 2) * 4 + 1) * 9 : Lc + LINK_YB + (bx + 2 * bz) * 9;
+            const float4* Lzf = Lc + (sib * 4 + 2) * 9;
+            const float4* Lzb = bz ? Lc + ((sib - 4) * 4 + 2) * 9 : Lc + LINK_ZB + (bx + 2 * by) * 9;
+            const float4* Ltf = Lc + (sib * 4 + 3) * 9;
+            const float4* Ltb = Lm + (sib * 4 + 3) * 9;
 
             float2 acc[12], H[12];
 #pragma unroll
@@ -325,23 +287,17 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
                 }
             }
         }
-        // this warp is done with spinor plane rel-1 and link plane rel; the last of the eight warps
-        // refills both slots: spinor plane rel+3, link plane rel+2
+        // this warp is done with plane rel-1; the last of the eight warps reuses its slot for rel+2
         __syncwarp();
-        int last = 0;
         if (lane == 0) {
             __threadfence_block();
-            last = (atomicAdd(&s_out[rel % WRING], 1) & 7) == 7;
-            if (last) __threadfence_block();
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last && !s_fail) {
-            const int np = rel + 3 < nrel ? rel + 3 : -1;
-            const int nl = rel + 2 <= nrel - 2 ? rel + 2 : -1;
-            if (np >= 0 || nl >= 0) {
-                if (lane == 0) tc::fence_proxy_async();
-                __syncwarp();
-                issue(np, nl);
+            const int before = atomicAdd(&s_out[(rel - 1) % WRING], 1);
+            if ((before & 7) == 7) {
+                __threadfence_block();
+                if (!s_fail && rel + 2 < nrel) {
+                    tc::fence_proxy_async();
+                    issue(rel + 2);
+                }
             }
         }
     }
@@ -349,17 +305,12 @@ __global__ void __launch_bounds__(256, 2) k_fsweep_w(const __grid_constant__ CUt
     if (tid == 0 && s_fail) {
         // wait (bounded) for the last copy issued into each slot before the CTA exits
         const long long d2 = clock64() + a.wait_limit;
-        const int hi = s_issued, lhi = s_lissued;
+        const int hi = s_issued;
         for (int b = 0; b < WRING; ++b) {
-            int lastp = -1;
+            int last = -1;
             for (int r = b; r <= hi; r += WRING)
-                if (r + 1 != a.skip_copy) lastp = r;
-            if (lastp >= 0) tc::mbar_wait(&full[b], (uint32_t)((lastp / WRING) & 1), d2);
-        }
-        for (int b = 0; b < WLRING; ++b) {
-            int lastl = -1;
-            for (int q = b + 1; q <= lhi; q += WLRING) lastl = q;
-            if (lastl >= 1) tc::mbar_wait(&lfull[b], (uint32_t)(((lastl - 1) / WLRING) & 1), d2);
+                if (r + 1 != a.skip_copy) last = r;
+            if (last >= 0) tc::mbar_wait(&full[b], (uint32_t)((last / WRING) & 1), d2);
         }
         atomicExch(err, 1);
     }
@@ -398,9 +349,6 @@ int launch_one(const CUtensorMap& map, const Geom4& g, int gx, int* err, cudaStr
     static bool attr = false;   // one flag per instantiation
     if (!attr) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
-        // the warp-per-site form needs the whole shared-memory carveout for its two CTAs per SM
-        if (W && cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-            return 1;
         attr = true;
     }
     kern<<<dim3(gx * (NB / TW)), threads, smem, s>>>(map, g, err);

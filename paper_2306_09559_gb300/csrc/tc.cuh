@@ -57,12 +57,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
         "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// L2 prefetch of one box of a tensor map (no completion to wait for: a hint to the memory system).
-__device__ __forceinline__ void tma_prefetch_2d(const void* tmap, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)tmap), "r"(x),
-                 "r"(y)
-                 : "memory");
-}
 // Plain (untiled) bulk copy global -> shared: both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
