@@ -154,9 +154,20 @@ def test_per_noise_matvec_accounting_table4():
 
 
 def test_statistics():
+    """Values worked by hand: mean (6 + 2i)/4; real deviations -0.5, 0.5, 2.5, -2.5 (squares
+    sum to 13, over n - 1 = 3); complex deviations with |.|^2 = 0.5, 2.5, 6.5, 8.5 (sum 18)."""
     s = np.array([1 + 1j, 2 - 1j, 4 + 0j, -1 + 2j])
     st = M.statistics(s)
-    assert st["mean"] == s.mean()
-    assert np.isclose(st["var_re"], np.var([1, 2, 4, -1], ddof=1))
-    assert np.isclose(st["var_complex"], np.sum(np.abs(s - s.mean()) ** 2) / 3)
-    assert np.isclose(st["se_re"], np.sqrt(st["var_re"] / 4))
+    assert st["n"] == 4
+    assert st["mean"] == 1.5 + 0.5j
+    assert np.isclose(st["var_re"], 13.0 / 3.0, rtol=1e-15)
+    assert np.isclose(st["var_complex"], 6.0, rtol=1e-15)
+    assert np.isclose(st["se_re"], np.sqrt(13.0 / 12.0), rtol=1e-15)
+    # a constant shift leaves the variances alone; a factor c scales the complex one by |c|^2
+    sh = M.statistics(s + (3 - 7j))
+    assert np.isclose(sh["var_re"], 13.0 / 3.0) and np.isclose(sh["var_complex"], 6.0)
+    sc = M.statistics((2 - 1j) * s)
+    assert np.isclose(sc["var_complex"], 5 * 6.0)
+    # one sample: no variance
+    one = M.statistics(np.array([2 + 1j]))
+    assert one["mean"] == 2 + 1j and np.isnan(one["var_re"]) and np.isnan(one["se_re"])
