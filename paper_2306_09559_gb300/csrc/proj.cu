@@ -5,6 +5,8 @@
 // form H (setup), D and b^H Z D per noise column, and the rank-k updates
 // r = b - (A Z) D and x += Z D.  Vectors are in block layout
 // [site][spin*3 + colour][column] like the stencil's.
+#include <type_traits>
+
 #include "device.cuh"
 #include "kernels.h"
 #include "stencil.cuh"
@@ -25,6 +27,26 @@ template <class S> __device__ __forceinline__ double2 ld_d(const S* p) {
 
 // part[split][i*ky + j] = sum over the split's sites, e of conj(X[site][e][i]) s_e Y[site][e][j]
 // (s_e = gamma5 sign when g5 != 0), accumulated in FP64.
+// Double-float accumulation (FP32 hi + lo pair, error-free transformations; Dekker 1971, Knuth's
+// TwoSum): acc += a * b with the product split exactly into p + e (fmaf) and the sum hi + p
+// split exactly into s + err.  The pair carries about 48 bits of the running sum, so a Gram
+// entry of FP32 (or BF16) inputs is accurate to the FP64 level at FP32-pipe cost, where
+// GB300's FP64 units run at about 1/70 of its FP32 rate.  The _rn intrinsics keep the
+// compiler from contracting the additions into FMAs, which would break the transformations.
+struct DF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void mac(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <class SX, class SY>
 __global__ void k_block_gram(int V, const SX* __restrict__ X, int kx, const SY* __restrict__ Y, int ky, int g5,
                              double2* part, int nsplit) {
@@ -34,6 +56,30 @@ __global__ void k_block_gram(int V, const SX* __restrict__ X, int kx, const SY* 
     const int split = blockIdx.y;
     const int chunk = (V + nsplit - 1) / nsplit;
     const int s0 = split * chunk, s1 = min(V, s0 + chunk);
+    if constexpr (!std::is_same<SX, double>::value && !std::is_same<SY, double>::value) {
+        // FP32 / BF16 inputs (exact in FP32): double-float sums, a fresh pair per site (24
+        // products each) whose value is then added in FP64
+        double ar = 0, ai = 0;
+        for (int site = s0; site < s1; ++site) {
+            DF sr, si;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) {
+                const size_t row = (size_t)site * 12 + e;
+                const auto x = ld(X + (row * kx + i) * 2);
+                auto y = ld(Y + (row * ky + j) * 2);
+                const float yr = (g5 && e >= 6) ? -(float)y.re : (float)y.re;
+                const float yi = (g5 && e >= 6) ? -(float)y.im : (float)y.im;
+                sr.mac((float)x.re, yr);
+                sr.mac((float)x.im, yi);
+                si.mac((float)x.re, yi);
+                si.mac(-(float)x.im, yr);
+            }
+            ar += sr.value();
+            ai += si.value();
+        }
+        part[(size_t)split * kx * ky + idx] = make_double2(ar, ai);
+        return;
+    }
     double ar = 0, ai = 0;
     for (int site = s0; site < s1; ++site) {
 #pragma unroll
