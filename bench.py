@@ -502,11 +502,15 @@ FORM_SOURCES = {
     "k_fsweep_lsm": ("stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh", "tc.cuh"),
     "k_fsweep_w": ("stencil_fsweep_w.cuh", "stencil_fsweep.cuh", "stencil_fast.cuh", "stencil.cuh", "device.cuh",
                    "tc.cuh"),
+    "k_fsweep_p": ("stencil_fsweep_p.cuh", "stencil_fsweep_w.cuh", "stencil_fsweep.cuh", "stencil_fast.cuh",
+                   "stencil.cuh", "device.cuh", "tc.cuh"),
 }
 
 
 def fsweep_form(sweep_mask):
     """Name of the t-sweep form a sweep option mask in effect runs (mpmc_get_option)."""
+    if sweep_mask & 64:
+        return "k_fsweep_p"
     return "k_fsweep_w" if sweep_mask & 32 else "k_fsweep_lsm" if sweep_mask & 16 else "k_fsweep"
 
 

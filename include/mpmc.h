@@ -313,7 +313,7 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * the mask in effect for the current block width (0 where they do not
  * apply).
  * MPMC_OPT_FAST_SITES: sites per thread of those kernels (1 .. 16, default 1).
- * MPMC_OPT_SWEEP_STENCIL (mask 0 .. 63, default 55): t-sweep form of the
+ * MPMC_OPT_SWEEP_STENCIL (mask 0 .. 127, default 55): t-sweep form of the
  * stencil steps whose input is a stored block, on handles whose x, y, z
  * extents are even: a CTA walks t over a 2 x 2 x 2 block of sites and a
  * tile of right-hand sides, with the block's spinor planes staged in shared
@@ -326,11 +326,15 @@ MPMC_API int mpmc_autotune(mpmc_handle h, int max_nb, int steps);
  * sides, three CTAs per SM); bit 32: the warp-per-site form of that kernel
  * (tiles of 32 right-hand sides, one warp per site of the block, a ring of
  * three planes, no CTA-wide barrier per plane; blocks of 32 or more columns,
- * others run the bit-16 form).  Same arithmetic per site as the non-sweep
+ * others run the bit-16 form); bit 64: the two-sites-per-warp form (tiles
+ * of 16 right-hand sides, each warp holding the block's two x-sites, one
+ * per half-warp, so that one 16-byte link load serves both; a ring of three
+ * planes, no CTA-wide barrier per plane, four CTAs per SM; opt-in).  Same
+ * arithmetic per site as the non-sweep
  * kernel; the order in which the eight hops are summed and the order of the
  * FP64 per-block dot sums differ.  mpmc_autotune times the forms the mask
  * allows and keeps the fastest; mpmc_get_option returns the mask in effect
- * (class bits, plus 16 or 32 for the form that runs at the current block).
+ * (class bits, plus 16, 32 or 64 for the form that runs at the current block).
  * MPMC_OPT_SWEEP_ORDER (default 1): order in which the t-sweep CTAs take the
  * (2 x 2 x 2 site block, t-segment) pairs: 0 blocks in row order (x fastest)
  * for each segment in turn; 1 the segments of one block one after another,

@@ -122,8 +122,9 @@ void fast_geometry(const Geom& g, FastArgs& a);
 // made by fsweep_make_map; accumulator rows cfg.rows.
 // var: 0 links read from global memory (tile width min(nb, 32)); 1 each plane's links staged in
 // shared memory with its spinor rows (tile width 16); 2 warp-per-site form with staged links (tile
-// width 32, nb >= 32; nb = 16 runs variant 1).  fsweep_variant maps the sweep option mask (bit 4:
-// staged links, bit 5: warp-per-site) and nb to var; fsweep_tile gives its tile width.
+// width 32, nb >= 32; nb = 16 runs variant 1); 3 two-sites-per-warp form with staged links (tile
+// width 16).  fsweep_variant maps the sweep option mask (bit 4: staged links, bit 5: warp-per-site,
+// bit 6: two sites per warp) and nb to var; fsweep_tile gives its tile width.
 bool fsweep_supported(int storage, const Geom& g, int nb);
 int fsweep_variant(int mask, int nb);
 int fsweep_tile(int var, int nb);

@@ -110,7 +110,8 @@ struct mpmc_ctx {
     // first step), bit 1 undotted steps (inner steps of composite chains), bit 2 outer steps.
     int use_sweep = 55;           // bits 0-2: t-sweep form of the issue-lean kernels per class; bit 3: k_sweep;
                                   // bit 4: that form with each plane's links staged in shared memory;
-                                  // bit 5: its warp-per-site form (blocks of 32 or more columns)
+                                  // bit 5: its warp-per-site form (blocks of 32 or more columns);
+                                  // bit 6: its two-sites-per-warp form
     int sweep_ts = 0;
     int use_fast = 7;             // issue-lean kernels per class (FP32 / BF16S, block widths 16 .. 1024)
     int fast_sl = 1;              // sites per thread of the issue-lean kernels
@@ -426,7 +427,7 @@ int step_launch(mpmc_ctx* h, Workspace& ws, const StepArgs& a, const NoiseSpec& 
         f.alpha[0] = (float)a.alpha[0];
         f.alpha[1] = (float)a.alpha[1];
         const int var = fsweep_variant(h->use_sweep, ws.nb);
-        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, var == 1 ? 2 : 1)
+        const void* fmap = (ws.fsweep && (h->use_sweep & cls) && kind < 2) ? sweep_map(h, ws, a.in, var == 1 || var == 3 ? 2 : 1)
                                                                             : nullptr;
         prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
@@ -481,7 +482,7 @@ int outer_launch(mpmc_ctx* h, Workspace& ws, const OuterArgs& o, const NoiseSpec
             f.gamma[i] = (float)o.gamma[i];
         }
         const int var = fsweep_variant(h->use_sweep, ws.nb);
-        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, var == 1 ? 2 : 1) : nullptr;
+        const void* fmap = (ws.fsweep && (h->use_sweep & 4)) ? sweep_map(h, ws, o.in, var == 1 || var == 3 ? 2 : 1) : nullptr;
         prof_variant(h, fmap ? PROF_K_FSWEEP : PROF_K_FAST);
         if (fmap) {
             if (launch_fsweep(ws.storage, ws.nb, o.dot ? 4 : 3, f, ws.fsw, fmap, h->d_err, h->stream, var))
@@ -2166,9 +2167,9 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
                 consider(per);
             }
             if (!rc && (user_sweep & 1) && fsweep_supported(h->storage, h->g, nb)) {
-                // t-sweep form, with links read from global memory, (bit 16) staged with the planes
-                // and (bit 32) staged, one warp per site
-                for (int v : {0, 16, 32}) {
+                // t-sweep form, with links read from global memory, (bit 16) staged with the planes,
+                // (bit 32) staged, one warp per site, and (bit 64) staged, two sites per warp
+                for (int v : {0, 16, 32, 64}) {
                     if (v && !(user_sweep & v)) continue;
                     if (v == 32 && fsweep_variant(32, nb) != 2) continue;
                     h->use_sweep = 1 | v;
@@ -2193,7 +2194,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
     if (!rc && bnb == 0) rc = fail(h, MPMC_ENOMEM, "no block size fits the memory budget");
     // phase 2: at that width, the undotted and outer classes choose among the site-parallel
     // kernel, the issue-lean kernel and its t-sweep form with the parameters found above
-    int fast_mask = bfast & 1, sweep_mask = bsweep & 57;
+    int fast_mask = bfast & 1, sweep_mask = bsweep & 121;
     if (!rc) {
         h->tune_R = bR; h->tune_bx = bbx; h->tune_sl = bsl;
         h->fast_sl = bfsl;
@@ -2207,7 +2208,7 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
             for (int c = 0; c < 3 && !rc; ++c) {
                 if ((c >= 1 && !can_fast) || (c == 2 && !can_sweep)) continue;
                 h->use_fast = c >= 1 ? bit : 0;
-                h->use_sweep = (c == 2 ? bit | (bsweep & 48) : 0) | (bsweep & 8);
+                h->use_sweep = (c == 2 ? bit | (bsweep & 112) : 0) | (bsweep & 8);
                 double per;
                 if (time_class(bnb, cls, &per)) break;
                 if (per < bper) { bper = per; bf = c >= 1; bs = c == 2; }
@@ -2244,14 +2245,14 @@ int mpmc_autotune(mpmc_handle h, int max_nb, int steps) {
         const int shapes[][3] = {{bR, bbx, bsl}, {1, 32, 2}, {1, 64, 1}, {2, 32, 1}};
         for (const auto& sh : shapes)
             for (int fm : {0, 1, 3, 5, 7})
-                for (int sm : {0, 7, 23, 39}) {
+                for (int sm : {0, 7, 23, 39, 71}) {
                     if (sm && !fsw) continue;
                     if (fm == 7 && sh != shapes[0]) continue;   // no site-parallel step left to shape
                     // the links-staged t-sweep forms (bits 16, 32) only with the shape found in phase 1
-                    if (sm > 7 && (sh != shapes[0] || !(user_sweep & sm & 48) || !(fm & 7))) continue;
+                    if (sm > 7 && (sh != shapes[0] || !(user_sweep & sm & 112) || !(fm & 7))) continue;
                     if (sm == 39 && fsweep_variant(32, bnb) != 2) continue;
                     const int f = fm & user_fast;
-                    const int sw = (sm & f & user_sweep) | (sm & user_sweep & 48) | (bsweep & 8);
+                    const int sw = (sm & f & user_sweep) | (sm & user_sweep & 112) | (bsweep & 8);
                     cand.push_back({f, sw, sh[0], sh[1], sh[2]});
                 }
         double tbest = INFINITY;
@@ -2298,7 +2299,7 @@ int mpmc_set_option(mpmc_handle h, int option, int value) {
             h->use_tc = value != 0;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_STENCIL:
-            if (value < 0 || value > 63) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 63");
+            if (value < 0 || value > 127) return fail(h, MPMC_EINVAL, "sweep option is a mask in 0 .. 127");
             h->use_sweep = value;
             return MPMC_OK;
         case MPMC_OPT_SWEEP_SEGMENT:
@@ -2347,7 +2348,7 @@ int mpmc_get_option(mpmc_handle h, int option, int* value) {
             if (sweep_supported(h->storage, h->g, cur_nb(h))) v |= h->use_sweep & 8;
             if (v & 7) {
                 const int var = fsweep_variant(h->use_sweep, cur_nb(h));
-                v |= var == 2 ? 32 : var == 1 ? 16 : 0;
+                v |= var == 3 ? 64 : var == 2 ? 32 : var == 1 ? 16 : 0;
             }
             *value = v;
             return MPMC_OK;

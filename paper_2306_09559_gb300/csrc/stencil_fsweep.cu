@@ -1,6 +1,7 @@
 // Host side of the t-sweep issue-lean stencil kernels (stencil_fsweep.cuh); their
-// instantiations are split over stencil_fsweep_{f32,bf16,w_f32,w_bf16}.cu so that they compile
-// in parallel.
+// instantiations are split over stencil_fsweep_{f32,bf16,w_f32,w_bf16,p_f32,p_bf16}.cu so that
+// they compile in parallel.
+#include "stencil_fsweep_p.cuh"
 #include "stencil_fsweep_w.cuh"
 
 #include <algorithm>
@@ -15,18 +16,19 @@ bool fsweep_supported(int storage, const Geom& g, int nb) {
 }
 
 int fsweep_variant(int mask, int nb) {
+    if (mask & 64) return 3;
     if (mask & 32) return nb >= 32 ? 2 : 1;
     return (mask & 16) ? 1 : 0;
 }
 
-int fsweep_tile(int var, int nb) { return var == 2 ? fsw::WTW : var == 1 ? 16 : (nb < 32 ? nb : 32); }
+int fsweep_tile(int var, int nb) { return var == 2 ? fsw::WTW : var == 3 ? fsw::PTW : var == 1 ? 16 : (nb < 32 ? nb : 32); }
 
 SweepCfg fsweep_config(const Geom& g, int nb, int ts, int var) {
     SweepCfg c;
     const int tw = fsweep_tile(var, nb);
     c.nblk = (g.lx / 2) * (g.ly / 2) * (g.lz / 2);
     c.tiles = nb / tw;
-    const int per_sm = var == 2 ? 2 : var == 1 ? 3 : 512 / (8 * tw);   // resident CTAs per SM
+    const int per_sm = var == 3 ? 4 : var == 2 ? 2 : var == 1 ? 3 : 512 / (8 * tw);   // resident CTAs per SM
     if (ts <= 0) {
         // the longest segment that still fills two waves of the 152 SMs
         ts = g.lt;
@@ -70,7 +72,7 @@ bool fsweep_make_map(void* map, int storage, const void* base, int V, int nb, in
 
 int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepCfg& c, const void* map, int* err,
                   cudaStream_t s, int var) {
-    if (!fast_supported(storage, nb) || var < 0 || var > 2) return 1;
+    if (!fast_supported(storage, nb) || var < 0 || var > 3) return 1;
     if (var == 2 && nb < 32) var = 1;
     if (c.tiles != nb / fsweep_tile(var, nb)) return 1;   // shape made for another variant
     fsw::Geom4 g;
@@ -80,9 +82,11 @@ int launch_fsweep(int storage, int nb, int kind, const FastArgs& a, const SweepC
     g.nseg = c.nseg;
     const CUtensorMap& m = *reinterpret_cast<const CUtensorMap*>(map);
     if (storage == ST_F32)
-        return var == 2 ? fsw::launch_w_f32(nb, kind, m, g, c.rows, err, s)
+        return var == 3 ? fsw::launch_p_f32(nb, kind, m, g, c.rows, err, s)
+             : var == 2 ? fsw::launch_w_f32(nb, kind, m, g, c.rows, err, s)
                         : fsw::launch_f32(var, nb, kind, m, g, c.rows, err, s);
-    return var == 2 ? fsw::launch_w_bf16(nb, kind, m, g, c.rows, err, s)
+    return var == 3 ? fsw::launch_p_bf16(nb, kind, m, g, c.rows, err, s)
+         : var == 2 ? fsw::launch_w_bf16(nb, kind, m, g, c.rows, err, s)
                     : fsw::launch_bf16(var, nb, kind, m, g, c.rows, err, s);
 }
 

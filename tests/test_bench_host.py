@@ -17,7 +17,7 @@ import bench  # noqa: E402
 
 
 @pytest.mark.parametrize("mask,form", [(7, "k_fsweep"), (23, "k_fsweep_lsm"), (39, "k_fsweep_w"),
-                                       (55, "k_fsweep_w"), (0, "k_fsweep")])
+                                       (55, "k_fsweep_w"), (0, "k_fsweep"), (71, "k_fsweep_p")])
 def test_fsweep_form(mask, form):
     assert bench.fsweep_form(mask) == form
 

@@ -110,12 +110,12 @@ def test_fast_matches_site_parallel_and_oracle(dims, bc_t, block, prec, sl):
                                              ((6, 4, 2, 5), -1, 16), ((4, 2, 6, 2), 1, 64)])
 @pytest.mark.parametrize("prec", [G.FP32, G.BF16S])
 @pytest.mark.parametrize("segment", [0, 1, 3])
-@pytest.mark.parametrize("sweep", [7, 23, 39])
+@pytest.mark.parametrize("sweep", [7, 23, 39, 71])
 def test_fast_sweep_matches_fast_and_oracle(dims, bc_t, block, prec, segment, sweep):
     """The t-sweep form (TMA-staged planes; sweep 23 also stages each plane's
     links in shared memory, sweep 39 runs the warp-per-site form of that at
-    blocks of 32 or more and the sweep-23 form below) against k_fast and the
-    oracle: same arithmetic per site up to the order of the hop sum and of the
+    blocks of 32 or more and the sweep-23 form below, sweep 71 the
+    two-sites-per-warp form) against k_fast and the oracle: same arithmetic per site up to the order of the hop sum and of the
     FP64 dot sums."""
     if segment > dims[3]:
         pytest.skip("segment longer than the lattice")
@@ -129,14 +129,14 @@ def test_fast_sweep_matches_fast_and_oracle(dims, bc_t, block, prec, segment, sw
 
 
 @pytest.mark.parametrize("block", [128, 256, 512, 1024])
-@pytest.mark.parametrize("mask", [0, 7, 23, 39])
+@pytest.mark.parametrize("mask", [0, 7, 23, 39, 71])
 def test_fast_wide_blocks(block, mask):
     """The block widths the 8^4 benchmark runs (512, 1024) and the ones between:
     issue-lean kernels (plain and t-sweep) against the site-parallel ones, and
     each against the oracle on the same noise (paired bound)."""
     dims = (4, 4, 2, 4)
     setup = _setup(dims, 1)
-    # none, t-sweep, t-sweep with links in shared memory, its warp-per-site form
+    # none, t-sweep, t-sweep with links in shared memory, its warp-per-site and two-sites-per-warp forms
     on, used = _trace(dims, 1, G.FP32, block, 7, 1, block, setup=setup, defl=False, sweep=mask)
     off, _ = _trace(dims, 1, G.FP32, block, 0, 1, block, setup=setup, defl=False)
     assert used[:2] == (7, mask)

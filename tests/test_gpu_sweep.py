@@ -78,7 +78,7 @@ def test_sweep_not_used_where_it_does_not_apply():
 def test_sweep_segment_range():
     with G.Handle(links((4, 4, 4, 4), "haar", 0, 0.3), 0.12, G.FP32, 1) as h:
         with pytest.raises(G.MpmcError):
-            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 64)
+            h.mpmc_set_option(G.OPT_SWEEP_STENCIL, 128)
         with pytest.raises(G.MpmcError) as e:
             h.mpmc_set_option(G.OPT_SWEEP_SEGMENT, 5)
         assert e.value.code == G.MPMC_EINVAL

@@ -39,9 +39,10 @@ def _handle(prec, Z, lam, pair, polys, block=16):
 
 
 @pytest.mark.parametrize("skip", [1, 2, 5])
-@pytest.mark.parametrize("sweep", [7, 23, 39])
+@pytest.mark.parametrize("sweep", [7, 23, 39, 71])
 def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_recovers(skip, sweep):
-    """Every t-sweep form (links from global memory, staged, warp-per-site with blocks of 32)."""
+    """Every t-sweep form (links from global memory, staged, warp-per-site with blocks of 32,
+    two sites per warp)."""
     from test_gpu_parity import small_setup
     op, polys, lam, Z, pair = small_setup()
     polys = fp32_polys(polys)
